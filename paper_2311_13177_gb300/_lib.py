@@ -1,0 +1,80 @@
+"""ctypes view of libprop.so (declarations mirror include/prop.h).
+
+Loading fails loudly when the library has not been built: there is no
+fallback implementation of any step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB
+
+c_int, c_float, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_float, ctypes.c_double,
+                                                ctypes.c_void_p, ctypes.c_size_t)
+
+PROP_OK = 0
+STATUS_NAMES = {0: "PROP_OK", 1: "PROP_ERR_INVALID_ARG", 2: "PROP_ERR_OOM", 3: "PROP_ERR_CUDA",
+                4: "PROP_ERR_TIMEOUT", 5: "PROP_ERR_BUSY", 6: "PROP_ERR_NOT_READY",
+                7: "PROP_ERR_CANCELLED", 8: "PROP_ERR_UNIMPLEMENTED"}
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("n", c_int), ("nf", c_int), ("delta", ctypes.POINTER(c_double)),
+                ("nblades", c_int), ("theta", ctypes.POINTER(c_double)), ("lines", c_int),
+                ("readout", c_int), ("nframes", c_int), ("blade_frame", ctypes.POINTER(c_int)),
+                ("kb_width", c_int), ("bin_chunk", c_int), ("device", c_int)]
+
+
+class ReconParamsC(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("lr", c_float), ("beta1", c_float), ("beta2", c_float),
+                ("eps", c_float), ("tv_xy", c_float), ("tv_t", c_float), ("tv_eps", c_float)]
+
+
+# name -> (restype, argtypes); every symbol include/prop.h declares.
+SIGNATURES = {
+    "prop_plan_create": (c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(c_void_p)]),
+    "prop_plan_destroy": (c_int, [c_void_p]),
+    "prop_plan_workspace_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "prop_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "prop_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "prop_reconstruct": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p,
+                                 ctypes.POINTER(c_double), c_void_p]),
+    "prop_reconstruct_host": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p,
+                                      ctypes.POINTER(c_double), c_void_p]),
+    "prop_loss_grad": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p, c_void_p,
+                               ctypes.POINTER(c_double), c_void_p]),
+    "prop_render": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "prop_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class PropError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libprop.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is not built; run paper_2311_13177_gb300.build.build()")
+            L = ctypes.CDLL(LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != PROP_OK:
+        raise PropError(status, where, lib().prop_last_error().decode(errors="replace"))

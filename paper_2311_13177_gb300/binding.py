@@ -1,0 +1,226 @@
+"""Thin Python binding of libprop with the C ABI's names.
+
+Argument marshalling only: torch tensors supply device pointers and the
+current CUDA stream, numpy arrays supply host buffers; every step of the
+operator, adjoint, loss and optimiser runs in libprop's kernels.
+
+Layouts (complex64): V [T, N, N, Nf] (index [t, i2, i1, f], x = i - N/2),
+y [B, L, R], image [T, N, N].
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from ._lib import PlanDesc, ReconParamsC, check, lib
+
+__all__ = ["Plan", "ReconParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
+           "prop_forward", "prop_adjoint", "prop_reconstruct", "prop_reconstruct_host",
+           "prop_loss_grad", "prop_render"]
+
+
+@dataclass
+class ReconParams:
+    iters: int = 20
+    lr: float = 1e-2
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    tv_xy: float = 1e-3
+    tv_t: float = 0.0
+    tv_eps: float = 1e-3
+
+    def c(self) -> ReconParamsC:
+        return ReconParamsC(int(self.iters), float(self.lr), float(self.beta1), float(self.beta2),
+                            float(self.eps), float(self.tv_xy), float(self.tv_t), float(self.tv_eps))
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dev_ptr(t: torch.Tensor, shape, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.complex64:
+        raise TypeError(f"{name} must be complex64, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A libprop plan (geometry tables + workspace on one device)."""
+
+    def __init__(self, N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        delta = np.ascontiguousarray(delta, dtype=np.float64)
+        if device is None:
+            device = torch.cuda.current_device()
+        self.N, self.L, self.R, self.T = int(N), int(L), int(R), int(T)
+        self.B, self.Nf = len(theta), len(delta)
+        self.device = torch.device("cuda", int(device))
+        bf_ptr = None
+        if blade_frame is not None:
+            self._bf = np.ascontiguousarray(blade_frame, dtype=np.int32)
+            bf_ptr = self._bf.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        desc = PlanDesc(self.N, self.Nf, delta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        self.B, theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.L, self.R,
+                        self.T, bf_ptr, 0, int(bin_chunk), int(device))
+        h = ctypes.c_void_p()
+        check(lib().prop_plan_create(ctypes.byref(desc), ctypes.byref(h)), "prop_plan_create")
+        self._h = h
+
+    # shapes
+    @property
+    def vol_shape(self):
+        return (self.T, self.N, self.N, self.Nf)
+
+    @property
+    def data_shape(self):
+        return (self.B, self.L, self.R)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("plan has been destroyed")
+        return self._h
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            check(lib().prop_plan_destroy(self._h), "prop_plan_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        check(lib().prop_plan_workspace_bytes(self.handle, ctypes.byref(v)), "prop_plan_workspace_bytes")
+        return int(v.value)
+
+    def forward(self, V: torch.Tensor, y: torch.Tensor = None, stream=None) -> torch.Tensor:
+        if y is None:
+            y = torch.empty(self.data_shape, dtype=torch.complex64, device=V.device)
+        check(lib().prop_forward(self.handle, _dev_ptr(V, self.vol_shape, "V"),
+                                 _dev_ptr(y, self.data_shape, "y"), _stream(stream)), "prop_forward")
+        return y
+
+    def adjoint(self, y: torch.Tensor, V: torch.Tensor = None, stream=None) -> torch.Tensor:
+        if V is None:
+            V = torch.empty(self.vol_shape, dtype=torch.complex64, device=y.device)
+        check(lib().prop_adjoint(self.handle, _dev_ptr(y, self.data_shape, "y"),
+                                 _dev_ptr(V, self.vol_shape, "V"), _stream(stream)), "prop_adjoint")
+        return V
+
+    def reconstruct(self, y: torch.Tensor, params: ReconParams, V: torch.Tensor = None, trace=True,
+                    stream=None):
+        """Run params.iters Adam iterations in place on V (zeros if None).
+
+        Returns (V, loss_trace numpy array or None)."""
+        if V is None:
+            V = torch.zeros(self.vol_shape, dtype=torch.complex64, device=y.device)
+        tr = np.zeros(max(params.iters, 1), dtype=np.float64) if trace else None
+        tr_ptr = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None
+        pc = params.c()
+        check(lib().prop_reconstruct(self.handle, _dev_ptr(y, self.data_shape, "y"), ctypes.byref(pc),
+                                     _dev_ptr(V, self.vol_shape, "V"), tr_ptr, _stream(stream)),
+              "prop_reconstruct")
+        return V, (tr[:params.iters] if trace else None)
+
+    def reconstruct_host(self, y: np.ndarray, params: ReconParams, V: np.ndarray = None, trace=False,
+                         stream=None):
+        """Host-buffer reconstruction (copies in, iterates, copies out). V is updated in place."""
+        if V is None:
+            V = np.zeros(self.vol_shape, dtype=np.complex64)
+        for a, shp, name in ((y, self.data_shape, "y"), (V, self.vol_shape, "V")):
+            if not (isinstance(a, (np.ndarray, torch.Tensor))):
+                raise TypeError(f"{name} must be a numpy array or a CPU tensor")
+        yp = _host_ptr(y, self.data_shape, "y")
+        vp = _host_ptr(V, self.vol_shape, "V")
+        tr = np.zeros(max(params.iters, 1), dtype=np.float64) if trace else None
+        tr_ptr = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None
+        pc = params.c()
+        check(lib().prop_reconstruct_host(self.handle, yp, ctypes.byref(pc), vp, tr_ptr, _stream(stream)),
+              "prop_reconstruct_host")
+        return V, (tr[:params.iters] if trace else None)
+
+    def loss_grad(self, y: torch.Tensor, params: ReconParams, V: torch.Tensor, grad: torch.Tensor = None,
+                  stream=None):
+        """(L(V), dL/dRe V + i dL/dIm V)."""
+        if grad is None:
+            grad = torch.empty(self.vol_shape, dtype=torch.complex64, device=V.device)
+        loss = ctypes.c_double()
+        pc = params.c()
+        check(lib().prop_loss_grad(self.handle, _dev_ptr(y, self.data_shape, "y"), ctypes.byref(pc),
+                                   _dev_ptr(V, self.vol_shape, "V"), _dev_ptr(grad, self.vol_shape, "grad"),
+                                   ctypes.byref(loss), _stream(stream)), "prop_loss_grad")
+        return float(loss.value), grad
+
+    def render(self, V: torch.Tensor, f_lo: int = 0, f_hi: int = None, out: torch.Tensor = None,
+               stream=None) -> torch.Tensor:
+        if f_hi is None:
+            f_hi = self.Nf
+        if out is None:
+            out = torch.empty((self.T, self.N, self.N), dtype=torch.complex64, device=V.device)
+        check(lib().prop_render(self.handle, _dev_ptr(V, self.vol_shape, "V"), int(f_lo), int(f_hi),
+                                _dev_ptr(out, (self.T, self.N, self.N), "image"), _stream(stream)),
+              "prop_render")
+        return out
+
+
+def _host_ptr(a, shape, name) -> ctypes.c_void_p:
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.complex64 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: need a contiguous CPU complex64 tensor of shape {shape}")
+        return ctypes.c_void_p(a.data_ptr())
+    if a.dtype != np.complex64 or not a.flags.c_contiguous or tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name}: need a C-contiguous complex64 array of shape {shape}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# Function-style aliases with the C ABI's names.
+def prop_plan_create(N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None) -> Plan:
+    return Plan(N, L, R, theta, delta, blade_frame, T, bin_chunk, device)
+
+
+def prop_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def prop_plan_workspace_bytes(plan: Plan) -> int:
+    return plan.workspace_bytes()
+
+
+def prop_forward(plan: Plan, V, y=None, stream=None):
+    return plan.forward(V, y, stream)
+
+
+def prop_adjoint(plan: Plan, y, V=None, stream=None):
+    return plan.adjoint(y, V, stream)
+
+
+def prop_reconstruct(plan: Plan, y, params, V=None, trace=True, stream=None):
+    return plan.reconstruct(y, params, V, trace, stream)
+
+
+def prop_reconstruct_host(plan: Plan, y, params, V=None, trace=False, stream=None):
+    return plan.reconstruct_host(y, params, V, trace, stream)
+
+
+def prop_loss_grad(plan: Plan, y, params, V, grad=None, stream=None):
+    return plan.loss_grad(y, params, V, grad, stream)
+
+
+def prop_render(plan: Plan, V, f_lo=0, f_hi=None, out=None, stream=None):
+    return plan.render(V, f_lo, f_hi, out, stream)

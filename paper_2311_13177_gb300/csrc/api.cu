@@ -1,0 +1,257 @@
+// C ABI entry points (declared in include/prop.h): argument checking,
+// chunk loops and the reconstruction iteration.  Every step of the
+// operator, its adjoint, the loss and the optimiser runs in this library's
+// kernels; the host only validates, enqueues and copies.
+#include "prop_internal.cuh"
+
+#include <cmath>
+#include <algorithm>
+
+namespace prop {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+prop_status fail(prop_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+prop_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return PROP_ERR_CUDA;
+}
+
+namespace {
+
+#define PROP_LAUNCH(call)                                   \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call);   \
+  } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// y = A V, or r = A V - y_meas with |r|^2 reduced into *sumsq.
+prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_meas, const Reducer* red,
+                         double* sumsq, cudaStream_t s) {
+  for (int c = 0; c < p.nchunks; ++c) {
+    const int f0 = c * p.chunk;
+    const int nb = std::min(p.chunk, p.Nf - f0);
+    const bool last = c == p.nchunks - 1;
+    PROP_LAUNCH(fft_forward_rows(p, V, f0, s));
+    PROP_LAUNCH(fft_forward_cols(p, s));
+    PROP_LAUNCH(interp(p, f0, nb, y, c == 0 ? y_meas : nullptr, c > 0, last ? red : nullptr, sumsq, s));
+  }
+  return PROP_OK;
+}
+
+// V = scale * (unscaled adjoint) of r; scale = 1/N gives A^H.
+prop_status adjoint_impl(Plan& p, const float2* r, float2* V, cudaStream_t s) {
+  const float scale = 1.0f / (float)p.N;
+  for (int c = 0; c < p.nchunks; ++c) {
+    const int f0 = c * p.chunk;
+    const int nb = std::min(p.chunk, p.Nf - f0);
+    PROP_LAUNCH(spread(p, f0, nb, r, s));
+    PROP_LAUNCH(fft_adjoint_cols(p, s));
+    PROP_LAUNCH(fft_adjoint_rows(p, V, f0, scale, s));
+  }
+  return PROP_OK;
+}
+
+prop_status check_params(const prop_recon_params* q) {
+  if (!q) return fail(PROP_ERR_INVALID_ARG, "params is NULL");
+  if (q->iters < 0) return fail(PROP_ERR_INVALID_ARG, "iters must be >= 0");
+  if (!(q->lr >= 0.f) || !(q->beta1 >= 0.f && q->beta1 < 1.f) || !(q->beta2 >= 0.f && q->beta2 < 1.f) ||
+      !(q->eps > 0.f))
+    return fail(PROP_ERR_INVALID_ARG, "Adam parameters out of range");
+  if (!(q->tv_eps > 0.f) || !(q->tv_xy >= 0.f) || !(q->tv_t >= 0.f) || !std::isfinite(q->tv_xy) ||
+      !std::isfinite(q->tv_t))
+    return fail(PROP_ERR_INVALID_ARG, "TV parameters out of range (weights >= 0, tv_eps > 0)");
+  return PROP_OK;
+}
+
+AdamArgs adam_args(const prop_recon_params* q, int k) {
+  AdamArgs a{};
+  const double bc1 = 1.0 - std::pow((double)q->beta1, k);
+  const double bc2 = 1.0 - std::pow((double)q->beta2, k);
+  a.lr_t = (float)(q->lr / bc1);
+  a.inv_bc2_sqrt = (float)(1.0 / std::sqrt(bc2));
+  a.beta1 = q->beta1;
+  a.beta2 = q->beta2;
+  a.eps = q->eps;
+  a.tv_xy = q->tv_xy;
+  a.tv_t = q->tv_t;
+  a.tv_eps = q->tv_eps;
+  a.gscale = 2.f;
+  return a;
+}
+
+prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* q, float2* V,
+                             double* trace_host, cudaStream_t s) {
+  prop_status st = plan_ensure_recon(&p, std::max(q->iters, 1));
+  if (st != PROP_OK) return st;
+  const size_t vbytes = p.vol_elems() * sizeof(float2);
+  PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
+  PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
+  float2* cur = V;
+  float2* nxt = p.vol2;
+  for (int k = 1; k <= q->iters; ++k) {
+    if ((st = forward_impl(p, cur, p.resid, y, &p.red_interp, p.scalars, s)) != PROP_OK) return st;
+    if ((st = adjoint_impl(p, p.resid, p.grad, s)) != PROP_OK) return st;
+    PROP_LAUNCH(tv_adam(p, cur, p.grad, p.adam_m, p.adam_v, nxt, adam_args(q, k), &p.red_tv, p.scalars,
+                        p.loss_dev + (k - 1), s));
+    std::swap(cur, nxt);
+  }
+  if (cur != V) PROP_CUDA(cudaMemcpyAsync(V, cur, vbytes, cudaMemcpyDeviceToDevice, s));
+  if (trace_host && q->iters > 0) {
+    PROP_CUDA(cudaMemcpyAsync(trace_host, p.loss_dev, sizeof(double) * q->iters, cudaMemcpyDeviceToHost, s));
+    PROP_CUDA(cudaStreamSynchronize(s));
+  }
+  return PROP_OK;
+}
+
+}  // namespace
+}  // namespace prop
+
+using namespace prop;
+
+extern "C" {
+
+const char* prop_last_error(void) { return g_last_error.c_str(); }
+
+prop_status prop_plan_create(const prop_plan_desc* desc, prop_plan* out) {
+  if (!out) return fail(PROP_ERR_INVALID_ARG, "plan_create: out is NULL");
+  *out = nullptr;
+  Plan* p = nullptr;
+  prop_status st = plan_build(desc, &p);
+  if (st != PROP_OK) return st;
+  prop_plan h = new (std::nothrow) prop_plan_s{p};
+  if (!h) {
+    plan_free(p);
+    return fail(PROP_ERR_OOM, "plan_create: host allocation failed");
+  }
+  *out = h;
+  return PROP_OK;
+}
+
+prop_status prop_plan_destroy(prop_plan plan) {
+  if (!plan) return PROP_OK;
+  {
+    DeviceGuard g(plan->p->device);
+    cudaDeviceSynchronize();
+    plan_free(plan->p);
+  }
+  delete plan;
+  return PROP_OK;
+}
+
+prop_status prop_plan_workspace_bytes(prop_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(PROP_ERR_INVALID_ARG, "workspace_bytes: null argument");
+  const Plan& p = *plan->p;
+  size_t recon = p.recon_bytes;
+  if (!p.recon_ready) {
+    recon = (size_t)p.M * sizeof(float2) + 4 * p.vol_elems() * sizeof(float2) +
+            2 * (size_t)(1 << 15) * sizeof(double) + 64 * sizeof(double) + 256;
+  }
+  *bytes = p.table_bytes + p.work_bytes + recon;
+  return PROP_OK;
+}
+
+prop_status prop_forward(prop_plan plan, const void* V_dev, void* y_dev, void* stream) {
+  if (!plan || !V_dev || !y_dev) return fail(PROP_ERR_INVALID_ARG, "forward: null argument");
+  if (!aligned16(V_dev) || !aligned16(y_dev)) return fail(PROP_ERR_INVALID_ARG, "forward: buffers must be 16-byte aligned");
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  return forward_impl(p, (const float2*)V_dev, (float2*)y_dev, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+prop_status prop_adjoint(prop_plan plan, const void* y_dev, void* V_dev, void* stream) {
+  if (!plan || !V_dev || !y_dev) return fail(PROP_ERR_INVALID_ARG, "adjoint: null argument");
+  if (!aligned16(V_dev) || !aligned16(y_dev)) return fail(PROP_ERR_INVALID_ARG, "adjoint: buffers must be 16-byte aligned");
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  return adjoint_impl(p, (const float2*)y_dev, (float2*)V_dev, (cudaStream_t)stream);
+}
+
+prop_status prop_reconstruct(prop_plan plan, const void* y_dev, const prop_recon_params* params, void* V_dev,
+                             double* loss_trace_host, void* stream) {
+  if (!plan || !y_dev || !V_dev) return fail(PROP_ERR_INVALID_ARG, "reconstruct: null argument");
+  if (!aligned16(V_dev) || !aligned16(y_dev)) return fail(PROP_ERR_INVALID_ARG, "reconstruct: buffers must be 16-byte aligned");
+  prop_status st = check_params(params);
+  if (st != PROP_OK) return st;
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  return reconstruct_impl(p, (const float2*)y_dev, params, (float2*)V_dev, loss_trace_host, (cudaStream_t)stream);
+}
+
+prop_status prop_reconstruct_host(prop_plan plan, const void* y_host, const prop_recon_params* params,
+                                  void* V_host, double* loss_trace_host, void* stream) {
+  if (!plan || !y_host || !V_host) return fail(PROP_ERR_INVALID_ARG, "reconstruct_host: null argument");
+  prop_status st = check_params(params);
+  if (st != PROP_OK) return st;
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vbytes = p.vol_elems() * sizeof(float2);
+  const size_t ybytes = (size_t)p.M * sizeof(float2);
+  if (!p.stage_y) {
+    PROP_CUDA(cudaMalloc((void**)&p.stage_y, ybytes));
+    p.recon_bytes += ybytes;
+  }
+  if (!p.stage_v) {
+    PROP_CUDA(cudaMalloc((void**)&p.stage_v, vbytes));
+    p.recon_bytes += vbytes;
+  }
+  PROP_CUDA(cudaMemcpyAsync(p.stage_y, y_host, ybytes, cudaMemcpyHostToDevice, s));
+  PROP_CUDA(cudaMemcpyAsync(p.stage_v, V_host, vbytes, cudaMemcpyHostToDevice, s));
+  st = reconstruct_impl(p, p.stage_y, params, p.stage_v, nullptr, s);
+  if (st != PROP_OK) return st;
+  PROP_CUDA(cudaMemcpyAsync(V_host, p.stage_v, vbytes, cudaMemcpyDeviceToHost, s));
+  if (loss_trace_host && params->iters > 0)
+    PROP_CUDA(cudaMemcpyAsync(loss_trace_host, p.loss_dev, sizeof(double) * params->iters,
+                              cudaMemcpyDeviceToHost, s));
+  PROP_CUDA(cudaStreamSynchronize(s));
+  return PROP_OK;
+}
+
+prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const prop_recon_params* params, const void* V_dev,
+                           void* grad_dev, double* loss_host, void* stream) {
+  if (!plan || !y_dev || !V_dev || !loss_host) return fail(PROP_ERR_INVALID_ARG, "loss_grad: null argument");
+  if (!aligned16(V_dev) || !aligned16(y_dev) || (grad_dev && !aligned16(grad_dev)))
+    return fail(PROP_ERR_INVALID_ARG, "loss_grad: buffers must be 16-byte aligned");
+  if (!params || !(params->tv_eps > 0.f) || !(params->tv_xy >= 0.f) || !(params->tv_t >= 0.f))
+    return fail(PROP_ERR_INVALID_ARG, "loss_grad: TV parameters out of range");
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  prop_status st = plan_ensure_recon(&p, 1);
+  if (st != PROP_OK) return st;
+  if ((st = forward_impl(p, (const float2*)V_dev, p.resid, (const float2*)y_dev, &p.red_interp, p.scalars, s)) != PROP_OK)
+    return st;
+  if ((st = adjoint_impl(p, p.resid, p.grad, s)) != PROP_OK) return st;
+  AdamArgs a{};
+  a.tv_xy = params->tv_xy;
+  a.tv_t = params->tv_t;
+  a.tv_eps = params->tv_eps;
+  a.gscale = 2.f;
+  float2* out = grad_dev ? (float2*)grad_dev : p.grad;
+  PROP_LAUNCH(tv_grad(p, (const float2*)V_dev, p.grad, out, a, &p.red_tv, p.scalars, p.scalars + 1, s));
+  PROP_CUDA(cudaMemcpyAsync(loss_host, p.scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PROP_CUDA(cudaStreamSynchronize(s));
+  return PROP_OK;
+}
+
+prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, void* image_dev, void* stream) {
+  if (!plan || !V_dev || !image_dev) return fail(PROP_ERR_INVALID_ARG, "render: null argument");
+  Plan& p = *plan->p;
+  if (f_lo < 0 || f_hi > p.Nf || f_lo >= f_hi) return fail(PROP_ERR_INVALID_ARG, "render: need 0 <= f_lo < f_hi <= nf");
+  DeviceGuard g(p.device);
+  PROP_LAUNCH(render(p, (const float2*)V_dev, f_lo, f_hi, (float2*)image_dev, (cudaStream_t)stream));
+  return PROP_OK;
+}
+
+}  // extern "C"

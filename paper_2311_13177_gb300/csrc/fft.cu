@@ -1,0 +1,441 @@
+// Batched shared-memory FFTs of the oversampled grid (no cuFFT).
+//
+// The 2N x 2N transform of every (frame, bin) slice is done as two passes of
+// 1-D transforms of length n = 2N along one axis, each CTA transforming a
+// tile of kFftCols = 16 lines that are adjacent in memory, so that every
+// global access of a warp covers two runs of 16 consecutive complex64
+// values (2 x 128 B, fully coalesced).  Bins are the fastest axis of every
+// array, so the "lines" of a pass are (u1, f) columns of the grid or the
+// bins of one image row.
+//
+// Each 1-D transform is a mixed-radix Stockham FFT (radices 8, 4, 2, 3):
+// pass p with radix R and stride Ns (product of the previous radices)
+// reads R values at stride n/R, multiplies by exp(-+2 pi i r (j mod Ns) /
+// (Ns R)), does an R-point DFT in registers and writes the results at
+// (j / Ns) Ns R + (j mod Ns) + r Ns.  The first pass reads global memory
+// directly (zero padding and deapodisation applied on the fly), the last
+// pass writes global memory directly (cropping and scaling applied on the
+// fly); intermediate passes exchange through shared memory in place.
+// Every thread holds E = 16 (n = 2^a) or 24 (n = 3 * 2^a) values per pass.
+#include "prop_internal.cuh"
+
+namespace prop {
+namespace {
+
+struct RadixPlan {
+  int count;
+  int r[8];
+};
+
+__host__ __device__ constexpr RadixPlan radix_plan(int n) {
+  RadixPlan p{0, {1, 1, 1, 1, 1, 1, 1, 1}};
+  int m = n, threes = 0;
+  while (m % 3 == 0) {
+    m /= 3;
+    ++threes;
+  }
+  while (m % 8 == 0) {
+    p.r[p.count++] = 8;
+    m /= 8;
+  }
+  if (m % 4 == 0) {
+    p.r[p.count++] = 4;
+    m /= 4;
+  }
+  if (m % 2 == 0) {
+    p.r[p.count++] = 2;
+    m /= 2;
+  }
+  for (int i = 0; i < threes; ++i) p.r[p.count++] = 3;
+  return p;
+}
+
+template <int NFFT>
+struct Shape {
+  static constexpr int E = (NFFT % 3 == 0) ? 24 : 16;  // values per thread
+  static constexpr int TPL = NFFT / E;                 // threads per line
+  static constexpr int THREADS = TPL * kFftCols;
+  static constexpr size_t SMEM = (size_t)NFFT * kFftCols * sizeof(float2) + NFFT * sizeof(float2);
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// z * (SIGN i)
+template <int SIGN>
+__device__ __forceinline__ float2 mul_si(float2 z) {
+  return SIGN > 0 ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
+
+// In-register DFTs X_k = sum_q v_q exp(SIGN 2 pi i q k / R).
+template <int R, int SIGN>
+struct Dft;
+
+template <int SIGN>
+struct Dft<2, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <int SIGN>
+struct Dft<4, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = mul_si<SIGN>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <int SIGN>
+struct Dft<8, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    constexpr float h = 0.70710678118654752f;  // 1/sqrt(2)
+    float2 a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = cadd(v[q], v[q + 4]);
+      b[q] = csub(v[q], v[q + 4]);
+    }
+    // b_q *= w^q, w = exp(SIGN i pi / 4)
+    {
+      float2 z = b[1];
+      b[1] = make_float2((z.x - SIGN * z.y) * h, (z.y + SIGN * z.x) * h);
+      b[2] = mul_si<SIGN>(b[2]);
+      z = b[3];
+      b[3] = make_float2((-z.x - SIGN * z.y) * h, (-z.y + SIGN * z.x) * h);
+    }
+    Dft<4, SIGN>::run(a);
+    Dft<4, SIGN>::run(b);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[2 * q] = a[q];
+      v[2 * q + 1] = b[q];
+    }
+  }
+};
+
+template <int SIGN>
+struct Dft<3, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    constexpr float s3 = 0.86602540378443865f;  // sqrt(3)/2
+    float2 t = cadd(v[1], v[2]);
+    float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    float2 d = mul_si<SIGN>(cscale(csub(v[1], v[2]), s3));
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, d);
+    v[2] = csub(m, d);
+  }
+};
+
+// One Stockham pass; recurses into the next pass at compile time.
+template <int NFFT, int SIGN, int PI, int NS, class In, class Out>
+__device__ __forceinline__ void fft_pass(float2* X, const float2* tw, int col, int tl, const In& in,
+                                         const Out& out) {
+  constexpr RadixPlan RP = radix_plan(NFFT);
+  constexpr int R = RP.r[PI];
+  constexpr int E = Shape<NFFT>::E;
+  constexpr int TPL = Shape<NFFT>::TPL;
+  constexpr int NB = E / R;
+  constexpr int STRIDE = NFFT / R;
+  constexpr bool FIRST = PI == 0;
+  constexpr bool LAST = PI == RP.count - 1;
+  static_assert(E % R == 0, "radix must divide the per-thread count");
+  float2 v[E];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int j = tl + TPL * q;
+    const int k = j % NS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int pos = j + r * STRIDE;
+      float2 x;
+      if constexpr (FIRST)
+        x = in(pos, col);
+      else
+        x = X[pos * kFftCols + col];
+      if constexpr (NS > 1) {
+        if (r > 0) {
+          float2 w = tw[r * k * (NFFT / (NS * R))];
+          if (SIGN > 0) w.y = -w.y;
+          x = cmul(x, w);
+        }
+      }
+      v[q * R + r] = x;
+    }
+    Dft<R, SIGN>::run(v + q * R);
+  }
+  if constexpr (!LAST) {
+    if constexpr (!FIRST) __syncthreads();  // every read of this pass is done
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = tl + TPL * q;
+      const int d = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) X[(d + r * NS) * kFftCols + col] = v[q * R + r];
+    }
+    __syncthreads();
+    fft_pass<NFFT, SIGN, PI + 1, NS * R>(X, tw, col, tl, in, out);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = tl + TPL * q;
+      const int d = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) out(d + r * NS, col, v[q * R + r]);
+    }
+  }
+}
+
+// Position p of a length-n line holds image index i = x + N/2 for
+// x = p (p < N/2) or x = p - n (p >= n - N/2); other positions are padding.
+__device__ __forceinline__ int image_index(int p, int N, int n) {
+  const int h = N >> 1;
+  if (p < h) return p + h;
+  if (p >= n - h) return p - (n - h);
+  return -1;
+}
+
+struct FftArgs {
+  const float2* src;
+  float2* dst;
+  const float* deapod;
+  const float2* twiddle;
+  int N, n, Nf;
+  int C;   // bin stride of the workspace (the plan's chunk)
+  int Cv;  // valid bins in this chunk (<= C)
+  int f0;
+  float scale;
+};
+
+enum Kind { kFwdRows = 0, kFwdCols = 1, kAdjCols = 2, kAdjRows = 3 };
+
+// Forward rows: V[t][i2][i1][f0 + f] * c(i1) c(i2), padded -> rows[t][i2][u1][f].
+struct InFwdRows {
+  const float2* V;
+  const float* dp;
+  int N, n, Nf, Cv, f0, fbase;
+  size_t row;  // (t*N + i2)
+  float c2;
+  __device__ float2 operator()(int pos, int col) const {
+    const int f = fbase + col;
+    const int i1 = image_index(pos, N, n);
+    if (f >= Cv || i1 < 0) return make_float2(0.f, 0.f);
+    float2 x = __ldg(&V[(row * N + i1) * Nf + f0 + f]);
+    return cscale(x, dp[i1] * c2);
+  }
+};
+struct OutFwdRows {
+  float2* rows;
+  int n, C, fbase;
+  size_t row;
+  __device__ void operator()(int pos, int col, float2 val) const {
+    const int f = fbase + col;
+    if (f < C) rows[(row * n + pos) * C + f] = val;
+  }
+};
+// Forward columns: rows[t][i2][q], padded along i2 -> grid[t][u2][q], q = u1*C + f.
+struct InFwdCols {
+  const float2* rows;
+  int N, n;
+  size_t nq, q, t;
+  __device__ float2 operator()(int pos, int col) const {
+    const int i2 = image_index(pos, N, n);
+    if (i2 < 0) return make_float2(0.f, 0.f);
+    return __ldg(&rows[(t * N + i2) * nq + q + col]);
+  }
+};
+struct OutFwdCols {
+  float2* grid;
+  int n;
+  size_t nq, q, t;
+  __device__ void operator()(int pos, int col, float2 val) const {
+    grid[(t * n + pos) * nq + q + col] = val;
+  }
+};
+// Adjoint columns: grid[t][u2][q] -> inverse FFT along u2, crop -> rows[t][i2][q].
+struct InAdjCols {
+  const float2* grid;
+  int n;
+  size_t nq, q, t;
+  __device__ float2 operator()(int pos, int col) const {
+    return __ldg(&grid[(t * n + pos) * nq + q + col]);
+  }
+};
+struct OutAdjCols {
+  float2* rows;
+  int N, n;
+  size_t nq, q, t;
+  __device__ void operator()(int pos, int col, float2 val) const {
+    const int i2 = image_index(pos, N, n);
+    if (i2 >= 0) rows[(t * N + i2) * nq + q + col] = val;
+  }
+};
+// Adjoint rows: rows[t][i2][u1][f] -> inverse FFT along u1, crop,
+// * scale c(i1) c(i2) -> out[t][i2][i1][f0 + f].
+struct InAdjRows {
+  const float2* rows;
+  int n, C, Cv, fbase;
+  size_t row;
+  __device__ float2 operator()(int pos, int col) const {
+    const int f = fbase + col;
+    if (f >= Cv) return make_float2(0.f, 0.f);
+    return __ldg(&rows[(row * n + pos) * C + f]);
+  }
+};
+struct OutAdjRows {
+  float2* out;
+  const float* dp;
+  int N, n, Nf, Cv, f0, fbase;
+  size_t row;
+  float c2;
+  __device__ void operator()(int pos, int col, float2 val) const {
+    const int f = fbase + col;
+    const int i1 = image_index(pos, N, n);
+    if (f < Cv && i1 >= 0) out[(row * N + i1) * Nf + f0 + f] = cscale(val, dp[i1] * c2);
+  }
+};
+
+template <int NFFT, int KIND>
+__global__ void __launch_bounds__(Shape<NFFT>::THREADS) fft_kernel(FftArgs a) {
+  extern __shared__ float2 smem[];
+  float2* X = smem;
+  float2* tw = smem + NFFT * kFftCols;
+  for (int i = threadIdx.x; i < NFFT; i += blockDim.x) tw[i] = a.twiddle[i];
+  __syncthreads();
+  const int col = threadIdx.x % kFftCols;
+  const int tl = threadIdx.x / kFftCols;
+  if constexpr (KIND == kFwdRows) {
+    const size_t row = blockIdx.y;  // t*N + i2
+    const int i2 = (int)(row % a.N);
+    const int fbase = blockIdx.x * kFftCols;
+    InFwdRows in{a.src, a.deapod, a.N, a.n, a.Nf, a.Cv, a.f0, fbase, row, a.deapod[i2]};
+    OutFwdRows out{a.dst, a.n, a.C, fbase, row};
+    fft_pass<NFFT, -1, 0, 1>(X, tw, col, tl, in, out);
+  } else if constexpr (KIND == kFwdCols) {
+    const size_t nq = (size_t)a.n * a.C;
+    InFwdCols in{a.src, a.N, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
+    OutFwdCols out{a.dst, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
+    fft_pass<NFFT, -1, 0, 1>(X, tw, col, tl, in, out);
+  } else if constexpr (KIND == kAdjCols) {
+    const size_t nq = (size_t)a.n * a.C;
+    InAdjCols in{a.src, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
+    OutAdjCols out{a.dst, a.N, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
+    fft_pass<NFFT, +1, 0, 1>(X, tw, col, tl, in, out);
+  } else {
+    const size_t row = blockIdx.y;
+    const int i2 = (int)(row % a.N);
+    const int fbase = blockIdx.x * kFftCols;
+    InAdjRows in{a.src, a.n, a.C, a.Cv, fbase, row};
+    OutAdjRows out{a.dst, a.deapod, a.N, a.n, a.Nf, a.Cv, a.f0, fbase, row, a.deapod[i2] * a.scale};
+    fft_pass<NFFT, +1, 0, 1>(X, tw, col, tl, in, out);
+  }
+}
+
+template <int NFFT>
+cudaError_t launch(int kind, const FftArgs& a, dim3 grid, cudaStream_t s) {
+  const size_t smem = Shape<NFFT>::SMEM;
+  const int threads = Shape<NFFT>::THREADS;
+  switch (kind) {
+    case kFwdRows: fft_kernel<NFFT, kFwdRows><<<grid, threads, smem, s>>>(a); break;
+    case kFwdCols: fft_kernel<NFFT, kFwdCols><<<grid, threads, smem, s>>>(a); break;
+    case kAdjCols: fft_kernel<NFFT, kAdjCols><<<grid, threads, smem, s>>>(a); break;
+    default: fft_kernel<NFFT, kAdjRows><<<grid, threads, smem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int NFFT>
+cudaError_t configure_n() {
+  const int smem = (int)Shape<NFFT>::SMEM;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kAdjCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  return cudaFuncSetAttribute(fft_kernel<NFFT, kAdjRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+#define PROP_FFT_SIZES(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+
+cudaError_t dispatch(int n, int kind, const FftArgs& a, dim3 grid, cudaStream_t s) {
+  switch (n) {
+#define CASE(v) \
+  case v: return launch<v>(kind, a, grid, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+FftArgs base_args(const Plan& p) {
+  FftArgs a{};
+  a.deapod = p.deapod;
+  a.twiddle = p.twiddle;
+  a.N = p.N;
+  a.n = p.n;
+  a.Nf = p.Nf;
+  a.C = p.chunk;
+  a.Cv = p.chunk;
+  a.f0 = 0;
+  a.scale = 1.f;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t fft_configure(int n) {
+  switch (n) {
+#define CASE(v) \
+  case v: return configure_n<v>();
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t fft_forward_rows(const Plan& p, const float2* V, int f0, cudaStream_t s) {
+  FftArgs a = base_args(p);
+  a.src = V;
+  a.dst = p.rows;
+  a.f0 = f0;
+  a.Cv = std::min(p.chunk, p.Nf - f0);
+  dim3 grid((a.C + kFftCols - 1) / kFftCols, p.T * p.N);
+  return dispatch(p.n, kFwdRows, a, grid, s);
+}
+
+cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s) {
+  FftArgs a = base_args(p);
+  a.src = p.rows;
+  a.dst = p.grid;
+  dim3 grid(p.n * p.chunk / kFftCols, p.T);
+  return dispatch(p.n, kFwdCols, a, grid, s);
+}
+
+cudaError_t fft_adjoint_cols(const Plan& p, cudaStream_t s) {
+  FftArgs a = base_args(p);
+  a.src = p.grid;
+  a.dst = p.rows;
+  dim3 grid(p.n * p.chunk / kFftCols, p.T);
+  return dispatch(p.n, kAdjCols, a, grid, s);
+}
+
+cudaError_t fft_adjoint_rows(const Plan& p, float2* out, int f0, float scale, cudaStream_t s) {
+  FftArgs a = base_args(p);
+  a.src = p.rows;
+  a.dst = out;
+  a.f0 = f0;
+  a.scale = scale;
+  a.Cv = std::min(p.chunk, p.Nf - f0);
+  dim3 grid((a.Cv + kFftCols - 1) / kFftCols, p.T * p.N);
+  return dispatch(p.n, kAdjRows, a, grid, s);
+}
+
+}  // namespace prop

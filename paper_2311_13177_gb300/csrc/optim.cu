@@ -1,0 +1,232 @@
+// Fused smoothed-TV gradient + Adam update, the TV/loss reduction, and the
+// spectral-sum render.
+//
+// Sec. 4.3 optimises the volume with Adam on the data term plus total
+// variation in space and (for dynamic series) time.  Per complex voxel V(x):
+//   TV terms sqrt(|d|^2 + eps^2) over forward differences d along x1, x2 and
+//   t (no wrap-around); the gradient of one term with respect to its upper
+//   end is d / sqrt(|d|^2 + eps^2) and minus that for its lower end;
+//   g = gscale * A^H r + tv_xy grad TV_xy + tv_t grad TV_t;
+//   per real component: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+//   V -= (lr / (1 - b1^k)) m / (sqrt(v) / sqrt(1 - b2^k) + eps).
+// The update reads Vin and writes Vout (ping-pong), because neighbours of a
+// voxel are read by other threads.  One thread per complex voxel, bins
+// fastest, so warps read and write contiguous runs.
+#include "prop_internal.cuh"
+
+namespace prop {
+namespace {
+
+constexpr int kOptThreads = 256;
+
+__device__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+struct OptArgs {
+  const float2* Vin;
+  const float2* g;
+  float2* m;
+  float2* v;
+  float2* out;  // Vout (Adam) or grad (gradient only)
+  double* partials;
+  unsigned int* counter;
+  const double* data_loss;
+  double* loss_out;
+  long nvox;
+  int N, Nf, T;
+  AdamArgs p;
+};
+
+// d / sqrt(|d|^2 + eps^2) and sqrt(|d|^2 + eps^2)
+__device__ __forceinline__ float2 tv_term(float2 d, float eps2, float* mag) {
+  const float s = fmaf(d.x, d.x, fmaf(d.y, d.y, eps2));
+  const float inv = rsqrtf(s);
+  *mag = s * inv;
+  return make_float2(d.x * inv, d.y * inv);
+}
+
+template <bool ADAM>
+__global__ void __launch_bounds__(kOptThreads) opt_kernel(OptArgs a) {
+  const float eps2 = a.p.tv_eps * a.p.tv_eps;
+  const long sx = a.Nf;
+  const long sy = (long)a.N * a.Nf;
+  const long st = (long)a.N * a.N * a.Nf;
+  float local = 0.f;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.nvox;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long r1 = idx / a.Nf;
+    const int i1 = (int)(r1 % a.N);
+    const long r2 = r1 / a.N;
+    const int i2 = (int)(r2 % a.N);
+    const int t = (int)(r2 / a.N);
+    const float2 x = a.Vin[idx];
+    float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
+    float mag, sxy = 0.f, stt = 0.f;
+    if (a.p.tv_xy != 0.f) {
+      if (i1 + 1 < a.N) {
+        const float2 nb = a.Vin[idx + sx];
+        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+        gxy.x -= q.x;
+        gxy.y -= q.y;
+        sxy += mag;
+      }
+      if (i1 > 0) {
+        const float2 nb = a.Vin[idx - sx];
+        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+        gxy.x += q.x;
+        gxy.y += q.y;
+      }
+      if (i2 + 1 < a.N) {
+        const float2 nb = a.Vin[idx + sy];
+        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+        gxy.x -= q.x;
+        gxy.y -= q.y;
+        sxy += mag;
+      }
+      if (i2 > 0) {
+        const float2 nb = a.Vin[idx - sy];
+        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+        gxy.x += q.x;
+        gxy.y += q.y;
+      }
+    }
+    if (a.p.tv_t != 0.f) {
+      if (t + 1 < a.T) {
+        const float2 nb = a.Vin[idx + st];
+        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+        gt.x -= q.x;
+        gt.y -= q.y;
+        stt += mag;
+      }
+      if (t > 0) {
+        const float2 nb = a.Vin[idx - st];
+        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+        gt.x += q.x;
+        gt.y += q.y;
+      }
+    }
+    local += a.p.tv_xy * sxy + a.p.tv_t * stt;
+    const float2 gd = a.g[idx];
+    float2 g;
+    g.x = fmaf(a.p.gscale, gd.x, fmaf(a.p.tv_xy, gxy.x, a.p.tv_t * gt.x));
+    g.y = fmaf(a.p.gscale, gd.y, fmaf(a.p.tv_xy, gxy.y, a.p.tv_t * gt.y));
+    if constexpr (ADAM) {
+      float2 mm = a.m[idx], vv = a.v[idx];
+      mm.x = fmaf(a.p.beta1, mm.x, (1.f - a.p.beta1) * g.x);
+      mm.y = fmaf(a.p.beta1, mm.y, (1.f - a.p.beta1) * g.y);
+      vv.x = fmaf(a.p.beta2, vv.x, (1.f - a.p.beta2) * g.x * g.x);
+      vv.y = fmaf(a.p.beta2, vv.y, (1.f - a.p.beta2) * g.y * g.y);
+      const float dx = sqrtf(vv.x) * a.p.inv_bc2_sqrt + a.p.eps;
+      const float dy = sqrtf(vv.y) * a.p.inv_bc2_sqrt + a.p.eps;
+      float2 nx;
+      nx.x = x.x - a.p.lr_t * (mm.x / dx);
+      nx.y = x.y - a.p.lr_t * (mm.y / dy);
+      a.m[idx] = mm;
+      a.v[idx] = vv;
+      a.out[idx] = nx;
+    } else {
+      a.out[idx] = g;
+    }
+  }
+  if (a.partials) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const double bs = block_sum_d((double)local, sh);
+    if (threadIdx.x == 0) {
+      a.partials[blockIdx.x] = bs;
+      __threadfence();
+      const unsigned prev = atomicAdd(a.counter, 1u);
+      last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double s = 0.0;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&a.partials[i]);
+      s = block_sum_d(s, sh);
+      if (threadIdx.x == 0) {
+        *a.loss_out = s + (a.data_loss ? __ldcg(a.data_loss) : 0.0);
+        *a.counter = 0u;
+      }
+    }
+  }
+}
+
+__global__ void render_kernel(const float2* V, float2* img, long npix, int Nf, int lo, int hi) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long)gridDim.x * blockDim.x) {
+    const float2* v = V + p * Nf;
+    float2 s = make_float2(0.f, 0.f);
+    for (int f = lo; f < hi; ++f) {
+      const float2 x = v[f];
+      s.x += x.x;
+      s.y += x.y;
+    }
+    img[p] = s;
+  }
+}
+
+unsigned opt_blocks(const Plan& p, const Reducer* red) {
+  long need = ((long)p.vol_elems() + kOptThreads - 1) / kOptThreads;
+  long cap = red ? std::min<long>(red->capacity, 16384) : 16384;
+  return (unsigned)std::max<long>(1, std::min(need, cap));
+}
+
+OptArgs make_args(const Plan& p, const float2* Vin, const float2* g, float2* out, const AdamArgs& aa,
+                  const Reducer* red, const double* data_loss, double* loss_out) {
+  OptArgs a{};
+  a.Vin = Vin;
+  a.g = g;
+  a.out = out;
+  a.partials = red ? red->partials : nullptr;
+  a.counter = red ? red->counter : nullptr;
+  a.data_loss = data_loss;
+  a.loss_out = loss_out;
+  a.nvox = (long)p.vol_elems();
+  a.N = p.N;
+  a.Nf = p.Nf;
+  a.T = p.T;
+  a.p = aa;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t tv_adam(const Plan& p, const float2* Vin, const float2* g, float2* m, float2* v, float2* Vout,
+                    const AdamArgs& aa, const Reducer* red, const double* data_loss, double* loss_out,
+                    cudaStream_t s) {
+  OptArgs a = make_args(p, Vin, g, Vout, aa, red, data_loss, loss_out);
+  a.m = m;
+  a.v = v;
+  opt_kernel<true><<<opt_blocks(p, red), kOptThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tv_grad(const Plan& p, const float2* V, const float2* g, float2* grad, const AdamArgs& aa,
+                    const Reducer* red, const double* data_loss, double* loss_out, cudaStream_t s) {
+  OptArgs a = make_args(p, V, g, grad, aa, red, data_loss, loss_out);
+  opt_kernel<false><<<opt_blocks(p, red), kOptThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t render(const Plan& p, const float2* V, int f_lo, int f_hi, float2* img, cudaStream_t s) {
+  const long npix = (long)p.T * p.N * p.N;
+  const unsigned blocks = (unsigned)std::min<long>((npix + 255) / 256, 16384);
+  render_kernel<<<blocks, 256, 0, s>>>(V, img, npix, p.Nf, f_lo, f_hi);
+  return cudaGetLastError();
+}
+
+}  // namespace prop

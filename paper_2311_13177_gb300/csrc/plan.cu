@@ -1,0 +1,346 @@
+// Plan builder: validates the geometry, computes every table in FP64 on the
+// host, stores them in FP32 on the device, and sizes the workspace.
+//
+// Tables (all from the operator y_b(k) = s sum_f P sum_x V exp(-2 pi i k.x)
+// evaluated by a Kaiser-Bessel NUFFT with oversampling 2 and width 6):
+//   * per sample m = (b L + l) R + j: k = k_r d_b + k_p d_b^perp, grid
+//     coordinate u = 2N k (mod 2N, exact because the sum over integer x is
+//     1-periodic in k), first tap floor(u) - 2 and the six weights per axis
+//     psi(u - tap), psi(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta);
+//   * deapodisation c(x) = I0(beta) / psihat(x / 2N) with the closed-form
+//     transform psihat(xi) = W sinh(sqrt(beta^2 - (pi W xi)^2)) / sqrt(...),
+//     beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8) (Beatty et al. 2005);
+//   * displacement phase P[j][f] = exp(-2 pi i k_r Delta_f), the argument
+//     k_r Delta_f reduced modulo 1 in FP64 before the cosine and sine
+//     (Sec. 3: a displacement along the readout is a phase linear in k_r);
+//   * FFT twiddles exp(-2 pi i q / 2N);
+//   * spread tile lists: for every frame and 16x16-cell grid tile, the
+//     samples whose 6x6 footprint touches the tile (CSR, ascending m).
+#include "prop_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+namespace prop {
+
+namespace {
+
+// Modified Bessel function of the first kind, order 0, from its power series
+// I0(z) = sum_k ((z/2)^(2k)) / (k!)^2 (all terms positive, so the partial sums
+// converge monotonically; 60 terms reach double precision for z <= 40).
+double bessel_i0(double z) {
+  const double q = 0.25 * z * z;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 60; ++k) {
+    term *= q / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+bool fft_size_supported(int n) {
+  static const int ok[] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+  for (int v : ok)
+    if (v == n) return true;
+  return false;
+}
+
+struct DevAlloc {
+  Plan* p;
+  size_t* counter;
+  template <class T>
+  prop_status operator()(T** ptr, size_t count, const char* what) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return fail(PROP_ERR_OOM, std::string("cudaMalloc failed for ") + what + ": " +
+                                    cudaGetErrorString(e));
+    }
+    *counter += count * sizeof(T);
+    return PROP_OK;
+  }
+};
+
+template <class T>
+prop_status upload(T* dst, const std::vector<T>& src) {
+  PROP_CUDA(cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PROP_OK;
+}
+
+}  // namespace
+
+void plan_free(Plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
+                  p->tile_off, p->tile_samples, p->grid, p->rows, p->resid, p->grad,
+                  p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
+                  p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
+                  p->red_tv.counter, p->stage_y, p->stage_v};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+prop_status plan_build(const prop_plan_desc* d, Plan** out) {
+  if (!d || !out) return fail(PROP_ERR_INVALID_ARG, "plan_create: null argument");
+  *out = nullptr;
+  const int N = d->n;
+  if (N < 8 || N > 512 || N % 8 != 0 || !fft_size_supported(2 * N))
+    return fail(PROP_ERR_INVALID_ARG,
+                "plan_create: n must be a multiple of 8 in [8, 512] with 2n = 2^a 3^b (n = " +
+                    std::to_string(N) + ")");
+  if (d->nf < 1 || d->nf > 4096) return fail(PROP_ERR_INVALID_ARG, "plan_create: nf out of range");
+  if (d->nblades < 1 || d->lines < 1 || d->readout < 1)
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: nblades, lines and readout must be >= 1");
+  if ((long long)d->nblades * d->lines * d->readout > (1LL << 30))
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: too many samples");
+  if (d->nframes < 1) return fail(PROP_ERR_INVALID_ARG, "plan_create: nframes must be >= 1");
+  if (!d->delta || !d->theta) return fail(PROP_ERR_INVALID_ARG, "plan_create: delta/theta is NULL");
+  if (d->kb_width != 0 && d->kb_width != kKbWidth)
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: kb_width must be 0 or 6");
+  if (d->bin_chunk < 0 || d->bin_chunk > kMaxChunk)
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: bin_chunk must be in [0, 64]");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
+    cudaGetLastError();
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: no such CUDA device");
+  }
+  for (int f = 0; f < d->nf; ++f)
+    if (!std::isfinite(d->delta[f])) return fail(PROP_ERR_INVALID_ARG, "plan_create: delta not finite");
+  for (int b = 0; b < d->nblades; ++b) {
+    if (!std::isfinite(d->theta[b])) return fail(PROP_ERR_INVALID_ARG, "plan_create: theta not finite");
+    if (d->blade_frame && (d->blade_frame[b] < 0 || d->blade_frame[b] >= d->nframes))
+      return fail(PROP_ERR_INVALID_ARG, "plan_create: blade_frame out of range");
+  }
+
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return fail(PROP_ERR_OOM, "plan_create: host allocation failed");
+  p->N = N;
+  p->n = 2 * N;
+  p->Nf = d->nf;
+  p->B = d->nblades;
+  p->L = d->lines;
+  p->R = d->readout;
+  p->T = d->nframes;
+  p->M = p->B * p->L * p->R;
+  p->device = d->device;
+  p->chunk = d->bin_chunk == 0 ? std::min(p->Nf, 32) : std::min(d->bin_chunk, p->Nf);
+  p->nchunks = (p->Nf + p->chunk - 1) / p->chunk;
+  p->tiles_per_side = p->n / kTile;
+  p->theta.assign(d->theta, d->theta + p->B);
+  p->delta.assign(d->delta, d->delta + p->Nf);
+  p->blade_frame.assign(p->B, 0);
+  if (d->blade_frame) p->blade_frame.assign(d->blade_frame, d->blade_frame + p->B);
+
+  DeviceGuard guard(p->device);
+  if (!guard.ok) {
+    plan_free(p);
+    return fail(PROP_ERR_CUDA, "plan_create: cudaSetDevice failed");
+  }
+
+  const int n = p->n;
+  const double W = kKbWidth, sigma = 2.0;
+  const double beta = M_PI * std::sqrt((W / sigma) * (W / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
+  const double i0b = bessel_i0(beta);
+
+  auto psi = [&](double t) {
+    double a = 2.0 * t / W;
+    double r = 1.0 - a * a;
+    if (r < 0.0) return 0.0;
+    return bessel_i0(beta * std::sqrt(r)) / i0b;
+  };
+
+  // Per-sample grid indices and weights.
+  std::vector<uint32_t> kb_idx(p->M);
+  std::vector<float4> kb_w((size_t)p->M * 3);
+  std::vector<int> first_tap(2 * (size_t)p->M);
+  for (int b = 0; b < p->B; ++b) {
+    const double c = std::cos(p->theta[b]), s = std::sin(p->theta[b]);
+    for (int l = 0; l < p->L; ++l) {
+      const double kp = ((double)l - p->L / 2.0) / N;
+      for (int j = 0; j < p->R; ++j) {
+        const double kr = ((double)j - p->R / 2.0) / N;
+        const double k[2] = {kr * c - kp * s, kr * s + kp * c};
+        const size_t m = ((size_t)b * p->L + l) * p->R + j;
+        float w[12];
+        int base[2];
+        for (int a = 0; a < 2; ++a) {
+          double u = n * k[a];
+          u -= n * std::floor(u / n);
+          if (u >= n) u -= n;
+          if (u < 0) u = 0;
+          const double fl = std::floor(u);
+          const double fr = u - fl;
+          base[a] = ((int)fl - 2 + n) % n;
+          for (int q = 0; q < kKbWidth; ++q) w[a * 6 + q] = (float)psi(fr + 2.0 - q);
+        }
+        kb_idx[m] = (uint32_t)base[0] | ((uint32_t)base[1] << 16);
+        first_tap[2 * m] = base[0];
+        first_tap[2 * m + 1] = base[1];
+        kb_w[3 * m + 0] = make_float4(w[0], w[1], w[2], w[3]);
+        kb_w[3 * m + 1] = make_float4(w[4], w[5], w[6], w[7]);
+        kb_w[3 * m + 2] = make_float4(w[8], w[9], w[10], w[11]);
+      }
+    }
+  }
+
+  // Deapodisation along one axis.
+  std::vector<float> deapod(N);
+  for (int i = 0; i < N; ++i) {
+    const double xi = (double)(i - N / 2) / n;
+    const double a = M_PI * W * xi;
+    const double z2 = beta * beta - a * a;
+    double ft;
+    if (z2 > 0) {
+      const double z = std::sqrt(z2);
+      ft = W * std::sinh(z) / z;
+    } else if (z2 < 0) {
+      const double z = std::sqrt(-z2);
+      ft = W * std::sin(z) / z;
+    } else {
+      ft = W;
+    }
+    deapod[i] = (float)(i0b / ft);
+  }
+
+  // Displacement phase per readout sample and bin.
+  std::vector<float2> phase((size_t)p->R * p->Nf);
+  for (int j = 0; j < p->R; ++j) {
+    const double kr = ((double)j - p->R / 2.0) / N;
+    for (int f = 0; f < p->Nf; ++f) {
+      double arg = kr * p->delta[f];
+      arg -= std::nearbyint(arg);
+      phase[(size_t)j * p->Nf + f] = make_float2((float)std::cos(2 * M_PI * arg),
+                                                 (float)-std::sin(2 * M_PI * arg));
+    }
+  }
+
+  std::vector<float2> tw(n);
+  for (int q = 0; q < n; ++q)
+    tw[q] = make_float2((float)std::cos(2 * M_PI * q / n), (float)-std::sin(2 * M_PI * q / n));
+
+  // Spread tile lists (counting sort by (frame, tile)).
+  const int tps = p->tiles_per_side;
+  const size_t ntile = (size_t)p->T * tps * tps;
+  std::vector<int> tile_off(ntile + 1, 0);
+  auto tiles_of = [&](int base, int* out_t) {
+    int cnt = 0;
+    for (int q = 0; q < kKbWidth; ++q) {
+      int t = ((base + q) % n) / kTile;
+      bool seen = false;
+      for (int z = 0; z < cnt; ++z) seen |= out_t[z] == t;
+      if (!seen) out_t[cnt++] = t;
+    }
+    return cnt;
+  };
+  for (size_t m = 0; m < (size_t)p->M; ++m) {
+    const int frame = p->blade_frame[m / ((size_t)p->L * p->R)];
+    int tr[2], tc[2];
+    const int nr = tiles_of(first_tap[2 * m + 1], tr);
+    const int nc = tiles_of(first_tap[2 * m], tc);
+    for (int a = 0; a < nr; ++a)
+      for (int c2 = 0; c2 < nc; ++c2) tile_off[((size_t)frame * tps + tr[a]) * tps + tc[c2] + 1]++;
+  }
+  for (size_t t = 0; t < ntile; ++t) tile_off[t + 1] += tile_off[t];
+  p->tile_entries = tile_off[ntile];
+  std::vector<int> tile_samples(std::max(p->tile_entries, 1));
+  {
+    std::vector<int> cursor(tile_off.begin(), tile_off.end() - 1);
+    for (size_t m = 0; m < (size_t)p->M; ++m) {
+      const int frame = p->blade_frame[m / ((size_t)p->L * p->R)];
+      int tr[2], tc[2];
+      const int nr = tiles_of(first_tap[2 * m + 1], tr);
+      const int nc = tiles_of(first_tap[2 * m], tc);
+      for (int a = 0; a < nr; ++a)
+        for (int c2 = 0; c2 < nc; ++c2) {
+          const size_t tile = ((size_t)frame * tps + tr[a]) * tps + tc[c2];
+          tile_samples[cursor[tile]++] = (int)m;
+        }
+    }
+  }
+
+  DevAlloc tab{p, &p->table_bytes};
+  DevAlloc wrk{p, &p->work_bytes};
+  prop_status st;
+#define TRY(x)               \
+  do {                       \
+    st = (x);                \
+    if (st != PROP_OK) {     \
+      plan_free(p);          \
+      return st;             \
+    }                        \
+  } while (0)
+  TRY(tab(&p->kb_idx, kb_idx.size(), "sample indices"));
+  TRY(tab(&p->kb_w, kb_w.size(), "sample weights"));
+  TRY(tab(&p->phase, phase.size(), "phase table"));
+  TRY(tab(&p->deapod, deapod.size(), "deapodisation table"));
+  TRY(tab(&p->twiddle, tw.size(), "twiddles"));
+  TRY(tab(&p->blade_frame_d, p->blade_frame.size(), "blade frames"));
+  TRY(tab(&p->tile_off, tile_off.size(), "tile offsets"));
+  TRY(tab(&p->tile_samples, tile_samples.size(), "tile samples"));
+  TRY(wrk(&p->grid, (size_t)p->T * n * n * p->chunk, "grid workspace"));
+  TRY(wrk(&p->rows, (size_t)p->T * N * n * p->chunk, "row workspace"));
+  TRY(upload(p->kb_idx, kb_idx));
+  TRY(upload(p->kb_w, kb_w));
+  TRY(upload(p->phase, phase));
+  TRY(upload(p->deapod, deapod));
+  TRY(upload(p->twiddle, tw));
+  TRY(upload(p->blade_frame_d, p->blade_frame));
+  TRY(upload(p->tile_off, tile_off));
+  TRY(upload(p->tile_samples, tile_samples));
+  {
+    cudaError_t e = fft_configure(n);
+    if (e == cudaSuccess) e = nufft_configure(p->chunk);
+    if (e != cudaSuccess) {
+      plan_free(p);
+      return cuda_fail(e, "fft_configure");
+    }
+  }
+#undef TRY
+  *out = p;
+  return PROP_OK;
+}
+
+prop_status plan_ensure_recon(Plan* p, int iters) {
+  DevAlloc rec{p, &p->recon_bytes};
+  prop_status st;
+  if (!p->recon_ready) {
+    const size_t nv = p->vol_elems();
+    const int red_cap = 1 << 15;
+    if ((st = rec(&p->resid, (size_t)p->M, "residual")) != PROP_OK) return st;
+    if ((st = rec(&p->grad, nv, "gradient")) != PROP_OK) return st;
+    if ((st = rec(&p->vol2, nv, "volume buffer")) != PROP_OK) return st;
+    if ((st = rec(&p->adam_m, nv, "Adam m")) != PROP_OK) return st;
+    if ((st = rec(&p->adam_v, nv, "Adam v")) != PROP_OK) return st;
+    if ((st = rec(&p->scalars, 8, "loss scalars")) != PROP_OK) return st;
+    if ((st = rec(&p->red_interp.partials, red_cap, "partials")) != PROP_OK) return st;
+    if ((st = rec(&p->red_interp.counter, 1, "counter")) != PROP_OK) return st;
+    if ((st = rec(&p->red_tv.partials, red_cap, "partials")) != PROP_OK) return st;
+    if ((st = rec(&p->red_tv.counter, 1, "counter")) != PROP_OK) return st;
+    p->red_interp.capacity = red_cap;
+    p->red_tv.capacity = red_cap;
+    PROP_CUDA(cudaMemset(p->red_interp.counter, 0, sizeof(unsigned int)));
+    PROP_CUDA(cudaMemset(p->red_tv.counter, 0, sizeof(unsigned int)));
+    p->recon_ready = true;
+  }
+  if (iters > p->loss_cap) {
+    if (p->loss_dev) {
+      cudaFree(p->loss_dev);
+      p->recon_bytes -= (size_t)p->loss_cap * sizeof(double);
+      p->loss_dev = nullptr;
+      p->loss_cap = 0;
+    }
+    const int cap = std::max(iters, 64);
+    if ((st = rec(&p->loss_dev, cap, "loss trace")) != PROP_OK) return st;
+    p->loss_cap = cap;
+  }
+  return PROP_OK;
+}
+
+}  // namespace prop

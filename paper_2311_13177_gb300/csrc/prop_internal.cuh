@@ -1,0 +1,145 @@
+// Internal declarations shared by the CUDA translation units of libprop.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/prop.h"
+
+namespace prop {
+
+constexpr int kKbWidth = 6;        // taps per axis of the Kaiser-Bessel kernel
+constexpr int kTile = 16;          // spread tile edge, grid cells
+constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
+constexpr int kMaxChunk = 64;      // most bins in one grid pass
+
+// Status plumbing -----------------------------------------------------------
+void set_error(const std::string& msg);
+prop_status fail(prop_status s, const std::string& msg);
+prop_status cuda_fail(cudaError_t e, const char* what);
+
+#define PROP_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t e__ = (call);                                    \
+    if (e__ != cudaSuccess) return ::prop::cuda_fail(e__, #call); \
+  } while (0)
+
+// Restores the caller's current device when it goes out of scope.
+struct DeviceGuard {
+  int old = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (old >= 0) cudaSetDevice(old);
+  }
+};
+
+// Deterministic "last block reduces" accumulator: every block writes one
+// double partial, the block that arrives last sums them in index order.
+struct Reducer {
+  double* partials = nullptr;      // [capacity]
+  unsigned int* counter = nullptr; // one word, returns to 0 after each use
+  int capacity = 0;
+};
+
+struct Plan {
+  // geometry
+  int N = 0, n = 0, Nf = 0, B = 0, L = 0, R = 0, T = 1, M = 0;
+  int chunk = 0;                 // bins per grid pass
+  int nchunks = 0;
+  int device = 0;
+  int tiles_per_side = 0;        // n / kTile
+  std::vector<double> theta, delta;
+  std::vector<int> blade_frame;
+
+  // device tables
+  uint32_t* kb_idx = nullptr;    // [M] packed (i1 | i2 << 16) first tap, mod n
+  float4* kb_w = nullptr;        // [M][3] -> 12 floats: w1[6] then w2[6]
+  float2* phase = nullptr;       // [R][Nf] exp(-2 pi i k_r Delta_f)
+  float* deapod = nullptr;       // [N]
+  float2* twiddle = nullptr;     // [n] exp(-2 pi i k / n)
+  int* blade_frame_d = nullptr;  // [B]
+  int* tile_off = nullptr;       // [T * tiles^2 + 1]
+  int* tile_samples = nullptr;   // [tile_off[end]]
+  int tile_entries = 0;
+
+  // grid workspace (one bin chunk)
+  float2* grid = nullptr;        // [T][n][n][chunk]
+  float2* rows = nullptr;        // [T][N][n][chunk] row-pass intermediate
+
+  // reconstruction state (allocated on first use)
+  bool recon_ready = false;
+  float2* resid = nullptr;       // [M]
+  float2* grad = nullptr;        // [T][N][N][Nf] adjoint of the residual
+  float2* vol2 = nullptr;        // [T][N][N][Nf] ping-pong volume
+  float2* adam_m = nullptr;      // [T][N][N][Nf] (re, im) first moment
+  float2* adam_v = nullptr;      // [T][N][N][Nf] (re, im) second moment
+  double* loss_dev = nullptr;    // [max_iters] loss trace
+  int loss_cap = 0;
+  double* scalars = nullptr;     // [4] data loss, tv_xy, tv_t scratch
+  Reducer red_interp, red_tv;
+
+  // host-API staging (allocated on first use)
+  float2* stage_y = nullptr;
+  float2* stage_v = nullptr;
+
+  size_t table_bytes = 0, work_bytes = 0, recon_bytes = 0;
+
+  size_t vol_elems() const { return (size_t)T * N * N * Nf; }
+};
+
+// plan.cu
+prop_status plan_build(const prop_plan_desc* d, Plan** out);
+void plan_free(Plan* p);
+prop_status plan_ensure_recon(Plan* p, int iters);
+
+// fft.cu: the four line-FFT passes of the 2-D (i)FFT per bin chunk.
+// Forward: V chunk -> rows (deapodise, pad, FFT along x1) -> grid (pad, FFT along x2).
+// Adjoint: grid -> rows (iFFT along u2, crop) -> out chunk (iFFT along u1, crop, deapodise, scale).
+cudaError_t fft_forward_rows(const Plan& p, const float2* V, int f0, cudaStream_t s);
+cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s);
+cudaError_t fft_adjoint_cols(const Plan& p, cudaStream_t s);
+cudaError_t fft_adjoint_rows(const Plan& p, float2* out, int f0, float scale, cudaStream_t s);
+cudaError_t fft_configure(int n);
+
+// nufft.cu
+// Interpolation of the grid chunk at every blade sample, times the
+// displacement phase, summed over the chunk's bins, scaled by s.
+// mode 0: y = part, 1: y += part; y_meas != null subtracts the measurement
+// (first chunk). With red != null the final |y|^2 is reduced into *sumsq.
+cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_meas,
+                   bool accumulate, const Reducer* red, double* sumsq, cudaStream_t s);
+// Tiled spread of conj(phase) * r into the grid chunk (every cell written).
+cudaError_t nufft_configure(int chunk);
+cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, cudaStream_t s);
+
+// optim.cu
+struct AdamArgs {
+  float lr_t;        // lr / (1 - beta1^k)
+  float inv_bc2_sqrt;// 1 / sqrt(1 - beta2^k)
+  float beta1, beta2, eps;
+  float tv_xy, tv_t, tv_eps;
+  float gscale;      // factor on the adjoint (2 for the squared-L2 data term)
+};
+// Fused smoothed-TV gradient + Adam: Vout = Adam(Vin, gscale*g + TV grads).
+// Writes data + tv_xy*TV_xy + tv_t*TV_t of Vin into loss_out[0] when red != null.
+cudaError_t tv_adam(const Plan& p, const float2* Vin, const float2* g, float2* m, float2* v,
+                    float2* Vout, const AdamArgs& a, const Reducer* red,
+                    const double* data_loss, double* loss_out, cudaStream_t s);
+// grad = gscale * g + TV grads (no update); loss as above.
+cudaError_t tv_grad(const Plan& p, const float2* V, const float2* g, float2* grad,
+                    const AdamArgs& a, const Reducer* red, const double* data_loss,
+                    double* loss_out, cudaStream_t s);
+cudaError_t render(const Plan& p, const float2* V, int f_lo, int f_hi, float2* img, cudaStream_t s);
+
+}  // namespace prop
+
+struct prop_plan_s {
+  prop::Plan* p;
+};

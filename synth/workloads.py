@@ -74,6 +74,11 @@ WORKLOADS = {
     # 32x32, 6 ellipses, Nf=8 over [-2, 2], 5 blades at 0..144 deg, 8 lines x 32.
     "tiny": Workload("tiny", N=32, Nf=8, delta_lo=-2.0, delta_hi=2.0, B=5, L=8, R=32,
                      n_ellipses=6, iters=20, lr=1e-2, tv_xy=1e-3),
+    # Small dynamic series the oracle runs in full: 32^2, Nf 4, 8 golden-angle
+    # blades over 4 frames (2 per frame), moving ellipse, temporal TV.
+    "dyn_small": Workload("dyn_small", N=32, Nf=4, delta_lo=-2.0, delta_hi=2.0, B=8, L=8, R=32,
+                          T=4, angles="golden", n_ellipses=6, iters=20, lr=1e-2, tv_xy=1e-3,
+                          tv_t=1e-2, motion=(0, 3.0, 4.0)),
     # Reduced static problem the oracle runs in full: 64^2, Nf 8, 8 blades.
     "small64": Workload("small64", N=64, Nf=8, delta_lo=-4.0, delta_hi=4.0, B=8, L=16, R=64,
                         n_ellipses=10, iters=100, lr=1e-2, tv_xy=1e-3),

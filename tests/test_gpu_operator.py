@@ -1,0 +1,113 @@
+"""GPU forward/adjoint through the C ABI against the FP64 oracle (<= 1e-4 rel L2)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import rel, geometry, random_case, workload_case
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4   # forward and adjoint, relative L2 against the exact NDFT
+
+
+def _plan(c, bin_chunk=0):
+    from paper_2311_13177_gb300 import Plan
+    return Plan(c["N"], c["L"], c["R"], c["theta"], c["delta"], c["blade_frame"], c["T"], bin_chunk=bin_chunk)
+
+
+def _check(c, bin_chunk=0):
+    g = geometry(c["N"], c["L"], c["R"], c["theta"], c["delta"], c["blade_frame"], c["T"])
+    plan = _plan(c, bin_chunk)
+    dev = torch.device("cuda")
+    y = plan.forward(torch.from_numpy(c["V"]).to(dev)).cpu().numpy()
+    y_ref = oracle.forward(c["V"].astype(np.complex128), g)
+    e1 = rel(y, y_ref)
+    V = plan.adjoint(torch.from_numpy(c["y"]).to(dev)).cpu().numpy()
+    V_ref = oracle.adjoint(c["y"].astype(np.complex128), g)
+    e2 = rel(V, V_ref)
+    plan.destroy()
+    assert e1 < TOL and e2 < TOL, (e1, e2)
+    return e1, e2
+
+
+@pytest.mark.parametrize("shape", [
+    (32, 8, 5, 8, 32, 1),     # tiny workload's shape
+    (64, 8, 8, 16, 64, 1),    # several tiles per side
+    (48, 3, 4, 6, 48, 1),     # 2N = 96 (radix 3), odd bin count
+    (24, 5, 3, 4, 24, 1),     # 2N = 48, ragged spread tiles are impossible (n % 16 == 0), odd R/L mix
+    (16, 2, 2, 16, 16, 2),    # two frames, L = N
+    (32, 1, 3, 5, 37, 1),     # single bin, odd readout count
+    (40, 1, 3, 5, 37, 1),     # 2N = 80 is not 2^a 3^b: rejected by plan creation
+])
+def test_forward_adjoint_match_oracle(shape):
+    N, Nf, B, L, R, T = shape
+    c = random_case(N, Nf, B, L, R, T, seed=N + Nf)
+    if 2 * N not in (16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024):
+        from paper_2311_13177_gb300._lib import PropError
+        with pytest.raises(PropError):
+            _plan(c)
+        return
+    _check(c)
+
+
+def test_chunked_grid_matches_unchunked():
+    """Bin chunks of 4 over Nf = 10 (ragged last chunk) recompute the grid per chunk."""
+    c = random_case(32, 10, 4, 6, 32, 2, seed=3)
+    _check(c, bin_chunk=4)
+
+
+def test_tiny_workload_both_operators():
+    w, p = workload_case("tiny")
+    p["V"] = np.random.default_rng(11).standard_normal((1, 32, 32, 8)).astype(np.complex64)
+    _check(p)
+
+
+def test_gpu_adjoint_identity_fp32():
+    from paper_2311_13177_gb300 import Plan
+    c = random_case(64, 8, 6, 8, 64, 2, seed=5)
+    plan = _plan(c)
+    dev = torch.device("cuda")
+    x = torch.from_numpy(c["V"]).to(dev)
+    y = torch.from_numpy(c["y"]).to(dev)
+    Ax = plan.forward(x)
+    Ahy = plan.adjoint(y)
+    lhs = torch.vdot(y.reshape(-1).to(torch.complex128), Ax.reshape(-1).to(torch.complex128))
+    rhs = torch.vdot(Ahy.reshape(-1).to(torch.complex128), x.reshape(-1).to(torch.complex128))
+    assert abs(complex(lhs - rhs)) < 1e-5 * abs(complex(lhs))
+    plan.destroy()
+
+
+@pytest.mark.parametrize("name", ["static", "dynamic"])
+def test_full_size_sampled_against_oracle(name):
+    """Full-size workloads in the bench's configuration: 4096 random samples of
+    A V and 512 random voxels of A^H y, each an independent exact sum."""
+    from paper_2311_13177_gb300 import Plan
+    w, p = workload_case(name)
+    g = geometry(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    rng = np.random.default_rng(7)
+    V = (rng.standard_normal((w.T, w.N, w.N, w.Nf)) + 1j * rng.standard_normal((w.T, w.N, w.N, w.Nf))).astype(np.complex64)
+    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    dev = torch.device("cuda")
+    y = plan.forward(torch.from_numpy(V).to(dev)).cpu().numpy().reshape(-1)
+    s = rng.choice(g.M, 4096, replace=False)
+    ref = oracle.forward_at(V.astype(np.complex128), g, s)
+    assert rel(y[s], ref) < TOL
+    yy = p["y"]
+    Va = plan.adjoint(torch.from_numpy(yy).to(dev)).cpu().numpy().reshape(-1)
+    q = rng.choice(Va.size, 512, replace=False)
+    refa = oracle.adjoint_at(yy.astype(np.complex128), g, q)
+    assert rel(Va[q], refa) < TOL
+    plan.destroy()
+
+
+def test_render_sums_bins():
+    from paper_2311_13177_gb300 import Plan
+    c = random_case(32, 6, 3, 4, 32, 2, seed=9)
+    plan = _plan(c)
+    V = torch.from_numpy(c["V"]).cuda()
+    img = plan.render(V).cpu().numpy()
+    assert np.allclose(img, oracle.render(c["V"]), atol=1e-5)
+    lo = plan.render(V, 0, 2).cpu().numpy()
+    assert np.allclose(lo, oracle.render(c["V"], 0, 2), atol=1e-5)
+    plan.destroy()

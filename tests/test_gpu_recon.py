@@ -1,0 +1,68 @@
+"""GPU loss, gradient and Adam reconstruction against the FP64 oracle.
+
+Bar: the volume after the same iterations within 1e-3 relative L2 of the
+oracle's; loss values within 1e-4; gradients within 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import rel, geometry, random_case, workload_case
+
+pytestmark = pytest.mark.gpu
+
+TOL_RECON = 1e-3
+TOL_GRAD = 1e-4
+
+
+def _params(w, iters):
+    from paper_2311_13177_gb300 import ReconParams
+    return (ReconParams(iters=iters, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps),
+            oracle.ReconParams(iters=iters, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps))
+
+
+@pytest.mark.parametrize("name,iters", [("tiny", 20), ("dyn_small", 20), ("small64", 100)])
+def test_reconstruction_matches_oracle(name, iters):
+    from paper_2311_13177_gb300 import Plan
+    w, p = workload_case(name)
+    g = geometry(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    pg, po = _params(w, iters)
+    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    V, tr = plan.reconstruct(torch.from_numpy(p["y"]).cuda(), pg)
+    Vo, tro = oracle.reconstruct(p["y"].astype(np.complex128), g, po)
+    e = rel(V.cpu().numpy(), Vo)
+    et = np.max(np.abs(tr - tro) / np.abs(tro))
+    plan.destroy()
+    assert e < TOL_RECON, e
+    assert et < 1e-4, et
+    assert tro[-1] < tro[0]
+
+
+def test_loss_and_gradient_match_oracle():
+    """Random volume, three frames of which the middle one has no blades."""
+    from paper_2311_13177_gb300 import Plan, ReconParams
+    c = random_case(48, 6, 5, 8, 48, T=3, seed=4)
+    c["blade_frame"] = np.array([0, 0, 2, 2, 2], dtype=np.int32)
+    g = geometry(48, 8, 48, c["theta"], c["delta"], c["blade_frame"], 3)
+    V = (c["V"] * np.float32(0.1)).astype(np.complex64)
+    pg = ReconParams(tv_xy=3e-2, tv_t=2e-2, tv_eps=5e-2)
+    po = oracle.ReconParams(tv_xy=3e-2, tv_t=2e-2, tv_eps=5e-2)
+    plan = Plan(48, 8, 48, c["theta"], c["delta"], c["blade_frame"], 3)
+    loss, grad = plan.loss_grad(torch.from_numpy(c["y"]).cuda(), pg, torch.from_numpy(V).cuda())
+    lo, go = oracle.loss_and_grad(V.astype(np.complex128), c["y"].astype(np.complex128), g, po)
+    plan.destroy()
+    assert abs(loss - lo) / abs(lo) < 1e-5
+    assert rel(grad.cpu().numpy(), go) < TOL_GRAD
+
+
+def test_host_api_matches_device_api():
+    from paper_2311_13177_gb300 import Plan, ReconParams
+    w, p = workload_case("tiny")
+    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    pg = ReconParams(iters=7, lr=w.lr, tv_xy=w.tv_xy)
+    Vd, trd = plan.reconstruct(torch.from_numpy(p["y"]).cuda(), pg)
+    Vh, trh = plan.reconstruct_host(p["y"].copy(), pg, trace=True)
+    plan.destroy()
+    assert rel(Vh, Vd.cpu().numpy()) < 1e-6
+    assert np.allclose(trh, trd, rtol=1e-6)

@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of the volumetric PROPELLER reconstruction step on GB300.
+
+A step is one full Adam iteration of the reconstruction (forward NUFFT with
+the displacement phase and bin sum, residual, adjoint NUFFT, fused TV
+gradient + Adam) over the static workload: a 256 x 256 image with 32
+spectral bins over [-4, 4] px, 16 uniformly rotated blades x 24 lines x 256
+readout samples, complex64 data from a seeded 20-ellipse water/fat phantom.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank reconstructs its
+own independent problem (weak scaling, no data-path collective); the
+barrier and the max over ranks use torch.distributed.
+
+Timing: W untimed steps, then K steps each bracketed by CUDA events on the
+library's stream, with a 256 MiB write between steps to flush L2.  The
+library's own per-stage events give the dominant kernel's duration for the
+roofline object.  `e2e` times the host-buffer API (prop_reconstruct_host)
+with its copies.  The reference arm times the FP64 CPU oracle on a bounded
+sample of the same step (see `cpu_baseline.sample`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "recon iters/s at 256²×32 bins×16 blades vs roofline; p50/p99 latency, mixed load"
+UNIT = "iters/s"
+WORKLOAD = "static"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(w) -> dict:
+    return {"workload": f"static {w.N}x{w.N} image, {w.Nf} bins over [{w.delta_lo:g},{w.delta_hi:g}] px, "
+                        f"{w.B} blades x {w.L} lines x {w.R} readout",
+            "N": w.N, "Nf": w.Nf, "blades": w.B, "lines": w.L, "readout": w.R, "frames": w.T,
+            "oversampling": 2, "kb_width": 6, "optimizer": "Adam lr 1e-2, TV_xy 1e-3"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# --- oracle timing (CPU baseline and the reference arm) ------------------------
+
+def oracle_sample(bins: int = 8):
+    """The static problem restricted to its first `bins` of 32 spectral bins.
+
+    The oracle's work per iteration is linear in the bin count (every bin is
+    an independent exact sum of the same size), so a step on this sample
+    costs bins/32 of a full step."""
+    import numpy as np
+    import oracle
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    p = synth.make_problem(w)
+    g = oracle.make_geometry(w.N, w.L, w.R, p["theta"], p["delta"][:bins], p["blade_frame"], w.T)
+    prm = oracle.ReconParams(lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
+    V = np.zeros((w.T, w.N, w.N, bins), dtype=np.complex128)
+    y = p["y"].astype(np.complex128)
+    return w, g, prm, V, y, w.Nf / bins
+
+
+def oracle_steps(n_steps: int, max_seconds: float, bins: int = 8):
+    import numpy as np
+    import oracle
+    w, g, prm, V, y, scale = oracle_sample(bins)
+    m = np.zeros(V.shape + (2,))
+    v = np.zeros(V.shape + (2,))
+    done = 0
+    t0 = time.perf_counter()
+    for k in range(1, n_steps + 1):
+        _, grad = oracle.loss_and_grad(V, y, g, prm)
+        V, m, v = oracle.adam_step(V, grad, m, v, k, prm)
+        done += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, scale
+
+
+def cpu_cores() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 0) for i in threadpool_info()), default=0)
+        if n:
+            return int(n)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline_obj(seconds: float = 20.0) -> dict:
+    done, dt, scale = oracle_steps(1000, seconds)
+    return {"value": done / (dt * scale), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{done} FP64 oracle iteration(s) (exact NDFT forward + explicit adjoint, TV, Adam) "
+                      f"on 8 of the 32 spectral bins of the static workload, {dt:.1f} s; "
+                      f"rate scaled by 8/32 (work is linear in bins)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    warm = min(args.warmup, 1)
+    if warm:
+        oracle_steps(warm, 60.0)
+    done, dt, scale = oracle_steps(max(1, args.steps), 120.0)
+    value = done / (dt * scale)
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "warmup": warm, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{done} oracle iteration(s) on 8 of 32 bins ({dt:.1f} s), "
+                                       f"scaled by 8/32; steps capped to fit 120 s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --- GPU arm ---------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stage_algo_bytes(plan) -> dict:
+    """Algorithmic bytes per launch of each stage (one bin chunk = all bins here).
+
+    |V| = 8 T N^2 Nf, |G| = 8 T (2N)^2 Nf, |y| = 8 B L R.  Per iteration they
+    sum to 9|V| + 4|G| + 3|y|: forward FFT reads V and writes G (split over
+    its row and column kernels as |V| and |G|), interpolation reads G and the
+    data and writes the residual, spread reads the residual and writes G,
+    the inverse FFT reads G and writes the gradient (|G| and |V|), TV + Adam
+    reads V, g, m, v and writes V, m, v."""
+    V = 8 * plan.T * plan.N * plan.N * plan.Nf
+    G = 8 * plan.T * (2 * plan.N) ** 2 * plan.Nf
+    y = 8 * plan.B * plan.L * plan.R
+    return {"fft_fwd_rows": V, "fft_fwd_cols": G, "interp": G + 2 * y, "spread": y + G,
+            "fft_adj_cols": G, "fft_adj_rows": V, "tv_adam": 7 * V}, 9 * V + 4 * G + 3 * y
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2311_13177_gb300 import build as _b
+    if rank == 0:
+        _b.build()
+    if world > 1:
+        dist.barrier()
+    import synth
+    from paper_2311_13177_gb300 import Plan, ReconParams
+
+    w = synth.WORKLOADS[WORKLOAD]
+    w_rank = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
+    prob = synth.make_problem(w_rank)
+    plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=local)
+    params = ReconParams(iters=1, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
+    y = torch.from_numpy(prob["y"]).to(dev)
+    Va = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)
+    Vb = torch.empty_like(Va)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    k = 0
+    for _ in range(args.warmup):
+        k += 1
+        plan.recon_step(y, params, k, Va, Vb, loss)
+        Va, Vb = Vb, Va
+    torch.cuda.synchronize()
+    plan.profile_read()  # discard warm-up records
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    plan.profile_enable(True)
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        k += 1
+        plan.recon_step(y, params, k, Va, Vb, loss)
+        ends[i].record(stream)
+        Va, Vb = Vb, Va
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    plan.profile_enable(False)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_sum = sum(step_ms) / 1000.0
+    prof = plan.profile_read()
+    final_loss = float(loss.item())
+
+    if world > 1:
+        tt = torch.tensor([t_sum], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_sum
+    value = world * K / t_max
+
+    # Back-to-back rate without L2 flushes (one reconstruct call of K iterations).
+    V0 = torch.zeros_like(Va)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.reconstruct(y, ReconParams(iters=K, lr=w.lr, tv_xy=w.tv_xy), V0, trace=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    warm_rate = K / (e0.elapsed_time(e1) / 1000.0)
+
+    # End to end through the host-buffer API: pinned y and V, copies inside.
+    y_h = torch.from_numpy(prob["y"]).pin_memory()
+    V_h = torch.zeros(plan.vol_shape, dtype=torch.complex64).pin_memory()
+    K_e2e = max(1, min(K, 2000))
+    plan.reconstruct_host(y_h, ReconParams(iters=3, lr=w.lr, tv_xy=w.tv_xy), V_h)  # staging warm-up
+    V_h.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.reconstruct_host(y_h, ReconParams(iters=K_e2e, lr=w.lr, tv_xy=w.tv_xy), V_h)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    vol_bytes = 8 * int(np.prod(plan.vol_shape))
+    y_bytes = 8 * int(np.prod(plan.data_shape))
+
+    if rank == 0:
+        algo, b_iter = stage_algo_bytes(plan)
+        stages = {k_: v_ for k_, v_ in prof.items() if v_[1] > 0}
+        dom = max(stages, key=lambda s: stages[s][0])
+        dom_ms = stages[dom][0] / stages[dom][1]
+        peak, peak_kind = measured_peaks()
+        achieved = algo[dom] / (dom_ms / 1000.0) / 1e9
+        traffic = None
+        tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tr_path):
+            with open(tr_path) as f:
+                traffic = json.load(f).get(dom)
+        launches = sum(v_[1] for v_ in prof.values())
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {**workload_config(w), "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel_ms": dom_ms, "algo_bytes_per_launch": algo[dom]},
+            "iteration_roofline": {"algo_bytes_per_iter": b_iter,
+                                   "achieved_gbs": b_iter * value / world / 1e9,
+                                   "frac": b_iter * value / world / 1e9 / peak,
+                                   "roofline_iters_per_s": peak * 1e9 / b_iter},
+            "stages_ms_per_step": {s: v_[0] / K for s, v_ in stages.items()},
+            "l2_warm_iters_per_s": warm_rate,
+            "e2e": {"value": world * K_e2e / t_e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": (y_bytes + vol_bytes) / K_e2e,
+                    "d2h_bytes_per_step": vol_bytes / K_e2e,
+                    "note": f"prop_reconstruct_host: one call of {K_e2e} iterations per rank, "
+                            f"pinned host y and V copied in and V copied out inside the timed region"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "final_loss": final_loss,
+            "wall_s": wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_obj()
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

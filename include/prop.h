@@ -134,6 +134,15 @@ PROP_API prop_status prop_adjoint(prop_plan plan, const void* y_dev, void* V_dev
 PROP_API prop_status prop_reconstruct(prop_plan plan, const void* y_dev, const prop_recon_params* params,
                              void* V_dev, double* loss_trace_host, void* stream);
 
+/* One Adam iteration of prop_reconstruct, out of place: V_out = the iterate
+ * after step k (1-based) from V_in (the two buffers must differ; alternate
+ * them between calls).  k == 1 resets the plan's Adam moments; later calls
+ * continue them, so steps k = 1, 2, ... must run in order on one plan.
+ * params->iters is ignored.  If loss_dev is non-NULL (device memory, one
+ * double) it receives L(V_in).  Does not synchronise. */
+PROP_API prop_status prop_recon_step(prop_plan plan, const void* y_dev, const prop_recon_params* params, int k,
+                                     const void* V_in_dev, void* V_out_dev, double* loss_dev, void* stream);
+
 /* prop_reconstruct on host buffers: copies y_host [B][L][R] and V_host
  * (start) to the device, runs K iterations, copies V back into V_host and
  * synchronises.  Staging buffers are allocated in the plan on first use.
@@ -154,6 +163,16 @@ PROP_API prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const pro
  * Requires 0 <= f_lo < f_hi <= Nf. */
 PROP_API prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, void* image_dev,
                         void* stream);
+
+/* Stage profiling.  Stages: 0 forward row FFT, 1 forward column FFT,
+ * 2 interpolation, 3 spread, 4 adjoint column FFT, 5 adjoint row FFT,
+ * 6 TV + Adam (or TV gradient), 7 other (render).  While enabled, every
+ * kernel launch of the plan is bracketed by two CUDA events on its stream. */
+#define PROP_NUM_STAGES 8
+PROP_API prop_status prop_profile_enable(prop_plan plan, int enable);
+/* Synchronises on the recorded events, writes per-stage total milliseconds
+ * and launch counts (arrays of PROP_NUM_STAGES), and clears the record. */
+PROP_API prop_status prop_profile_read(prop_plan plan, double* ms_out, long long* launches_out);
 
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 PROP_API const char* prop_last_error(void);

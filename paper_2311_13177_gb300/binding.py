@@ -59,7 +59,7 @@ def _dev_ptr(t: torch.Tensor, shape, name: str) -> ctypes.c_void_p:
 class Plan:
     """A libprop plan (geometry tables + workspace on one device)."""
 
-    def __init__(self, N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None):
+    def __init__(self, N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None, kb_width=0):
         theta = np.ascontiguousarray(theta, dtype=np.float64)
         delta = np.ascontiguousarray(delta, dtype=np.float64)
         if device is None:
@@ -73,7 +73,7 @@ class Plan:
             bf_ptr = self._bf.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         desc = PlanDesc(self.N, self.Nf, delta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         self.B, theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.L, self.R,
-                        self.T, bf_ptr, 0, int(bin_chunk), int(device))
+                        self.T, bf_ptr, int(kb_width), int(bin_chunk), int(device))
         h = ctypes.c_void_p()
         check(lib().prop_plan_create(ctypes.byref(desc), ctypes.byref(h)), "prop_plan_create")
         self._h = h
@@ -138,6 +138,20 @@ class Plan:
               "prop_reconstruct")
         return V, (tr[:params.iters] if trace else None)
 
+    def recon_step(self, y: torch.Tensor, params: ReconParams, k: int, V_in: torch.Tensor, V_out: torch.Tensor,
+                   loss: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """One Adam iteration k (1-based) from V_in into V_out; loss (float64 CUDA scalar) gets L(V_in)."""
+        lp = None
+        if loss is not None:
+            if not loss.is_cuda or loss.dtype != torch.float64 or loss.numel() < 1:
+                raise TypeError("loss must be a float64 CUDA tensor")
+            lp = ctypes.c_void_p(loss.data_ptr())
+        pc = params.c()
+        check(lib().prop_recon_step(self.handle, _dev_ptr(y, self.data_shape, "y"), ctypes.byref(pc), int(k),
+                                    _dev_ptr(V_in, self.vol_shape, "V_in"), _dev_ptr(V_out, self.vol_shape, "V_out"),
+                                    lp, _stream(stream)), "prop_recon_step")
+        return V_out
+
     def reconstruct_host(self, y: np.ndarray, params: ReconParams, V: np.ndarray = None, trace=False,
                          stream=None):
         """Host-buffer reconstruction (copies in, iterates, copies out). V is updated in place."""
@@ -179,6 +193,18 @@ class Plan:
         return out
 
 
+    def profile_enable(self, on: bool = True) -> None:
+        check(lib().prop_profile_enable(self.handle, 1 if on else 0), "prop_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{stage name: (total ms, launches)} since the last read (synchronises)."""
+        from ._lib import PROP_NUM_STAGES, STAGE_NAMES
+        ms = (ctypes.c_double * PROP_NUM_STAGES)()
+        n = (ctypes.c_longlong * PROP_NUM_STAGES)()
+        check(lib().prop_profile_read(self.handle, ms, n), "prop_profile_read")
+        return {STAGE_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(PROP_NUM_STAGES)}
+
+
 def _host_ptr(a, shape, name) -> ctypes.c_void_p:
     if isinstance(a, torch.Tensor):
         if a.is_cuda or a.dtype != torch.complex64 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
@@ -190,8 +216,8 @@ def _host_ptr(a, shape, name) -> ctypes.c_void_p:
 
 
 # Function-style aliases with the C ABI's names.
-def prop_plan_create(N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None) -> Plan:
-    return Plan(N, L, R, theta, delta, blade_frame, T, bin_chunk, device)
+def prop_plan_create(N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None, kb_width=0) -> Plan:
+    return Plan(N, L, R, theta, delta, blade_frame, T, bin_chunk, device, kb_width)
 
 
 def prop_plan_destroy(plan: Plan) -> None:

@@ -26,6 +26,35 @@ prop_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 namespace {
+cudaEvent_t take_event(Plan& p) {
+  if (!p.ev_pool.empty()) {
+    cudaEvent_t e = p.ev_pool.back();
+    p.ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+StageScope::StageScope(Plan& plan, int st, cudaStream_t stream) : p(plan), stage(st), s(stream) {
+  if (!p.profiling) return;
+  a = take_event(p);
+  b = take_event(p);
+  if (a) cudaEventRecord(a, s);
+}
+
+StageScope::~StageScope() {
+  if (!a || !b) return;
+  cudaEventRecord(b, s);
+  p.ev_rec[stage].emplace_back(a, b);
+}
+
+namespace {
 
 #define PROP_LAUNCH(call)                                   \
   do {                                                      \
@@ -42,22 +71,43 @@ prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_me
     const int f0 = c * p.chunk;
     const int nb = std::min(p.chunk, p.Nf - f0);
     const bool last = c == p.nchunks - 1;
-    PROP_LAUNCH(fft_forward_rows(p, V, f0, s));
-    PROP_LAUNCH(fft_forward_cols(p, s));
-    PROP_LAUNCH(interp(p, f0, nb, y, c == 0 ? y_meas : nullptr, c > 0, last ? red : nullptr, sumsq, s));
+    {
+      StageScope sc(p, kStFwdRows, s);
+      PROP_LAUNCH(fft_forward_rows(p, V, f0, s));
+    }
+    {
+      StageScope sc(p, kStFwdCols, s);
+      PROP_LAUNCH(fft_forward_cols(p, s));
+    }
+    {
+      StageScope sc(p, kStInterp, s);
+      // With a single chunk the residual is final here: also emit the spread's input.
+      float2* contrib = (y_meas && p.nchunks == 1) ? p.contrib : nullptr;
+      PROP_LAUNCH(interp(p, f0, nb, y, c == 0 ? y_meas : nullptr, c > 0, last ? red : nullptr, sumsq,
+                         contrib, s));
+    }
   }
   return PROP_OK;
 }
 
 // V = scale * (unscaled adjoint) of r; scale = 1/N gives A^H.
-prop_status adjoint_impl(Plan& p, const float2* r, float2* V, cudaStream_t s) {
+prop_status adjoint_impl(Plan& p, const float2* r, float2* V, bool contrib_ready, cudaStream_t s) {
   const float scale = 1.0f / (float)p.N;
   for (int c = 0; c < p.nchunks; ++c) {
     const int f0 = c * p.chunk;
     const int nb = std::min(p.chunk, p.Nf - f0);
-    PROP_LAUNCH(spread(p, f0, nb, r, s));
-    PROP_LAUNCH(fft_adjoint_cols(p, s));
-    PROP_LAUNCH(fft_adjoint_rows(p, V, f0, scale, s));
+    {
+      StageScope sc(p, kStSpread, s);
+      PROP_LAUNCH(spread(p, f0, nb, r, contrib_ready && p.nchunks == 1, s));
+    }
+    {
+      StageScope sc(p, kStAdjCols, s);
+      PROP_LAUNCH(fft_adjoint_cols(p, s));
+    }
+    {
+      StageScope sc(p, kStAdjRows, s);
+      PROP_LAUNCH(fft_adjoint_rows(p, V, f0, scale, s));
+    }
   }
   return PROP_OK;
 }
@@ -90,20 +140,32 @@ AdamArgs adam_args(const prop_recon_params* q, int k) {
   return a;
 }
 
+// One Adam iteration k (1-based): Vout = Adam step of L at Vin; L(Vin) -> *loss_dst.
+prop_status step_impl(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin,
+                      float2* Vout, double* loss_dst, cudaStream_t s) {
+  prop_status st;
+  if (k == 1) {
+    const size_t vbytes = p.vol_elems() * sizeof(float2);
+    PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
+    PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
+  }
+  if ((st = forward_impl(p, Vin, p.resid, y, &p.red_interp, p.scalars, s)) != PROP_OK) return st;
+  if ((st = adjoint_impl(p, p.resid, p.grad, true, s)) != PROP_OK) return st;
+  StageScope sc(p, kStOpt, s);
+  PROP_LAUNCH(tv_adam(p, Vin, p.grad, p.adam_m, p.adam_v, Vout, adam_args(q, k), &p.red_tv, p.scalars,
+                      loss_dst, s));
+  return PROP_OK;
+}
+
 prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* q, float2* V,
                              double* trace_host, cudaStream_t s) {
   prop_status st = plan_ensure_recon(&p, std::max(q->iters, 1));
   if (st != PROP_OK) return st;
   const size_t vbytes = p.vol_elems() * sizeof(float2);
-  PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
-  PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
   float2* cur = V;
   float2* nxt = p.vol2;
   for (int k = 1; k <= q->iters; ++k) {
-    if ((st = forward_impl(p, cur, p.resid, y, &p.red_interp, p.scalars, s)) != PROP_OK) return st;
-    if ((st = adjoint_impl(p, p.resid, p.grad, s)) != PROP_OK) return st;
-    PROP_LAUNCH(tv_adam(p, cur, p.grad, p.adam_m, p.adam_v, nxt, adam_args(q, k), &p.red_tv, p.scalars,
-                        p.loss_dev + (k - 1), s));
+    if ((st = step_impl(p, y, q, k, cur, nxt, p.loss_dev + (k - 1), s)) != PROP_OK) return st;
     std::swap(cur, nxt);
   }
   if (cur != V) PROP_CUDA(cudaMemcpyAsync(V, cur, vbytes, cudaMemcpyDeviceToDevice, s));
@@ -174,7 +236,7 @@ prop_status prop_adjoint(prop_plan plan, const void* y_dev, void* V_dev, void* s
   if (!aligned16(V_dev) || !aligned16(y_dev)) return fail(PROP_ERR_INVALID_ARG, "adjoint: buffers must be 16-byte aligned");
   Plan& p = *plan->p;
   DeviceGuard g(p.device);
-  return adjoint_impl(p, (const float2*)y_dev, (float2*)V_dev, (cudaStream_t)stream);
+  return adjoint_impl(p, (const float2*)y_dev, (float2*)V_dev, false, (cudaStream_t)stream);
 }
 
 prop_status prop_reconstruct(prop_plan plan, const void* y_dev, const prop_recon_params* params, void* V_dev,
@@ -186,6 +248,22 @@ prop_status prop_reconstruct(prop_plan plan, const void* y_dev, const prop_recon
   Plan& p = *plan->p;
   DeviceGuard g(p.device);
   return reconstruct_impl(p, (const float2*)y_dev, params, (float2*)V_dev, loss_trace_host, (cudaStream_t)stream);
+}
+
+prop_status prop_recon_step(prop_plan plan, const void* y_dev, const prop_recon_params* params, int k,
+                            const void* V_in_dev, void* V_out_dev, double* loss_dev, void* stream) {
+  if (!plan || !y_dev || !V_in_dev || !V_out_dev) return fail(PROP_ERR_INVALID_ARG, "recon_step: null argument");
+  if (V_in_dev == V_out_dev) return fail(PROP_ERR_INVALID_ARG, "recon_step: V_in and V_out must differ");
+  if (k < 1) return fail(PROP_ERR_INVALID_ARG, "recon_step: k must be >= 1");
+  if (!aligned16(V_in_dev) || !aligned16(V_out_dev) || !aligned16(y_dev))
+    return fail(PROP_ERR_INVALID_ARG, "recon_step: buffers must be 16-byte aligned");
+  prop_status st = check_params(params);
+  if (st != PROP_OK) return st;
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  if ((st = plan_ensure_recon(&p, 1)) != PROP_OK) return st;
+  return step_impl(p, (const float2*)y_dev, params, k, (const float2*)V_in_dev, (float2*)V_out_dev,
+                   loss_dev ? loss_dev : p.scalars + 2, (cudaStream_t)stream);
 }
 
 prop_status prop_reconstruct_host(prop_plan plan, const void* y_host, const prop_recon_params* params,
@@ -232,14 +310,17 @@ prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const prop_recon_p
   if (st != PROP_OK) return st;
   if ((st = forward_impl(p, (const float2*)V_dev, p.resid, (const float2*)y_dev, &p.red_interp, p.scalars, s)) != PROP_OK)
     return st;
-  if ((st = adjoint_impl(p, p.resid, p.grad, s)) != PROP_OK) return st;
+  if ((st = adjoint_impl(p, p.resid, p.grad, true, s)) != PROP_OK) return st;
   AdamArgs a{};
   a.tv_xy = params->tv_xy;
   a.tv_t = params->tv_t;
   a.tv_eps = params->tv_eps;
   a.gscale = 2.f;
   float2* out = grad_dev ? (float2*)grad_dev : p.grad;
-  PROP_LAUNCH(tv_grad(p, (const float2*)V_dev, p.grad, out, a, &p.red_tv, p.scalars, p.scalars + 1, s));
+  {
+    StageScope sc(p, kStOpt, s);
+    PROP_LAUNCH(tv_grad(p, (const float2*)V_dev, p.grad, out, a, &p.red_tv, p.scalars, p.scalars + 1, s));
+  }
   PROP_CUDA(cudaMemcpyAsync(loss_host, p.scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   PROP_CUDA(cudaStreamSynchronize(s));
   return PROP_OK;
@@ -250,7 +331,37 @@ prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, v
   Plan& p = *plan->p;
   if (f_lo < 0 || f_hi > p.Nf || f_lo >= f_hi) return fail(PROP_ERR_INVALID_ARG, "render: need 0 <= f_lo < f_hi <= nf");
   DeviceGuard g(p.device);
+  StageScope sc(p, kStOther, (cudaStream_t)stream);
   PROP_LAUNCH(render(p, (const float2*)V_dev, f_lo, f_hi, (float2*)image_dev, (cudaStream_t)stream));
+  return PROP_OK;
+}
+
+prop_status prop_profile_enable(prop_plan plan, int enable) {
+  if (!plan) return fail(PROP_ERR_INVALID_ARG, "profile_enable: null plan");
+  plan->p->profiling = enable != 0;
+  return PROP_OK;
+}
+
+prop_status prop_profile_read(prop_plan plan, double* ms_out, long long* launches_out) {
+  if (!plan) return fail(PROP_ERR_INVALID_ARG, "profile_read: null plan");
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  for (int st = 0; st < PROP_NUM_STAGES; ++st) {
+    double ms = 0.0;
+    for (auto& pr : p.ev_rec[st]) {
+      float t = 0.f;
+      PROP_CUDA(cudaEventSynchronize(pr.second));
+      PROP_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+      ms += t;
+    }
+    if (ms_out) ms_out[st] = ms;
+    if (launches_out) launches_out[st] = (long long)p.ev_rec[st].size();
+    for (auto& pr : p.ev_rec[st]) {
+      p.ev_pool.push_back(pr.first);
+      p.ev_pool.push_back(pr.second);
+    }
+    p.ev_rec[st].clear();
+  }
   return PROP_OK;
 }
 

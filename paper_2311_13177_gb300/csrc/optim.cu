@@ -18,6 +18,7 @@ namespace prop {
 namespace {
 
 constexpr int kOptThreads = 256;
+constexpr int kSeg = 1024;  // values per work unit
 
 __device__ double block_sum_d(double v, double* sh) {
 #pragma unroll
@@ -61,85 +62,93 @@ __device__ __forceinline__ float2 tv_term(float2 d, float eps2, float* mag) {
 
 template <bool ADAM>
 __global__ void __launch_bounds__(kOptThreads) opt_kernel(OptArgs a) {
+  // Work unit: a segment of kSeg consecutive values of one image row (t, i2);
+  // a row holds N * Nf values (i1, f).  Boundary tests use offsets within the
+  // row, so no per-value division is needed.
   const float eps2 = a.p.tv_eps * a.p.tv_eps;
-  const long sx = a.Nf;
-  const long sy = (long)a.N * a.Nf;
-  const long st = (long)a.N * a.N * a.Nf;
+  const int rowlen = a.N * a.Nf;
+  const int sx = a.Nf;
+  const long sy = rowlen;
+  const long st = (long)a.N * rowlen;
+  const int segs = (rowlen + kSeg - 1) / kSeg;
+  const long nseg = (long)a.T * a.N * segs;
   float local = 0.f;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.nvox;
-       idx += (long)gridDim.x * blockDim.x) {
-    const long r1 = idx / a.Nf;
-    const int i1 = (int)(r1 % a.N);
-    const long r2 = r1 / a.N;
-    const int i2 = (int)(r2 % a.N);
-    const int t = (int)(r2 / a.N);
-    const float2 x = a.Vin[idx];
-    float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
-    float mag, sxy = 0.f, stt = 0.f;
-    if (a.p.tv_xy != 0.f) {
-      if (i1 + 1 < a.N) {
-        const float2 nb = a.Vin[idx + sx];
-        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-        gxy.x -= q.x;
-        gxy.y -= q.y;
-        sxy += mag;
+  for (long sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
+    const long row = sgi / segs;
+    const int seg = (int)(sgi - row * segs);
+    const int i2 = (int)(row % a.N);
+    const int t = (int)(row / a.N);
+    const long rbase = row * rowlen;
+    for (int e = seg * kSeg + threadIdx.x; e < min(rowlen, (seg + 1) * kSeg); e += blockDim.x) {
+      const long idx = rbase + e;
+      const float2 x = a.Vin[idx];
+      float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
+      float mag, sxy = 0.f, stt = 0.f;
+      if (a.p.tv_xy != 0.f) {
+        if (e + sx < rowlen) {
+          const float2 nb = a.Vin[idx + sx];
+          const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+          gxy.x -= q.x;
+          gxy.y -= q.y;
+          sxy += mag;
+        }
+        if (e >= sx) {
+          const float2 nb = a.Vin[idx - sx];
+          const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+          gxy.x += q.x;
+          gxy.y += q.y;
+        }
+        if (i2 + 1 < a.N) {
+          const float2 nb = a.Vin[idx + sy];
+          const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+          gxy.x -= q.x;
+          gxy.y -= q.y;
+          sxy += mag;
+        }
+        if (i2 > 0) {
+          const float2 nb = a.Vin[idx - sy];
+          const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+          gxy.x += q.x;
+          gxy.y += q.y;
+        }
       }
-      if (i1 > 0) {
-        const float2 nb = a.Vin[idx - sx];
-        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-        gxy.x += q.x;
-        gxy.y += q.y;
+      if (a.p.tv_t != 0.f) {
+        if (t + 1 < a.T) {
+          const float2 nb = a.Vin[idx + st];
+          const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+          gt.x -= q.x;
+          gt.y -= q.y;
+          stt += mag;
+        }
+        if (t > 0) {
+          const float2 nb = a.Vin[idx - st];
+          const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+          gt.x += q.x;
+          gt.y += q.y;
+        }
       }
-      if (i2 + 1 < a.N) {
-        const float2 nb = a.Vin[idx + sy];
-        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-        gxy.x -= q.x;
-        gxy.y -= q.y;
-        sxy += mag;
+      local += a.p.tv_xy * sxy + a.p.tv_t * stt;
+      const float2 gd = a.g[idx];
+      float2 g;
+      g.x = fmaf(a.p.gscale, gd.x, fmaf(a.p.tv_xy, gxy.x, a.p.tv_t * gt.x));
+      g.y = fmaf(a.p.gscale, gd.y, fmaf(a.p.tv_xy, gxy.y, a.p.tv_t * gt.y));
+      if constexpr (ADAM) {
+        float2 mm = a.m[idx], vv = a.v[idx];
+        mm.x = fmaf(a.p.beta1, mm.x, (1.f - a.p.beta1) * g.x);
+        mm.y = fmaf(a.p.beta1, mm.y, (1.f - a.p.beta1) * g.y);
+        vv.x = fmaf(a.p.beta2, vv.x, (1.f - a.p.beta2) * g.x * g.x);
+        vv.y = fmaf(a.p.beta2, vv.y, (1.f - a.p.beta2) * g.y * g.y);
+        const float dx = sqrtf(vv.x) * a.p.inv_bc2_sqrt + a.p.eps;
+        const float dy = sqrtf(vv.y) * a.p.inv_bc2_sqrt + a.p.eps;
+        float2 nx;
+        nx.x = x.x - a.p.lr_t * (mm.x / dx);
+        nx.y = x.y - a.p.lr_t * (mm.y / dy);
+        a.m[idx] = mm;
+        a.v[idx] = vv;
+        a.out[idx] = nx;
+      } else {
+        a.out[idx] = g;
       }
-      if (i2 > 0) {
-        const float2 nb = a.Vin[idx - sy];
-        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-        gxy.x += q.x;
-        gxy.y += q.y;
-      }
-    }
-    if (a.p.tv_t != 0.f) {
-      if (t + 1 < a.T) {
-        const float2 nb = a.Vin[idx + st];
-        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-        gt.x -= q.x;
-        gt.y -= q.y;
-        stt += mag;
-      }
-      if (t > 0) {
-        const float2 nb = a.Vin[idx - st];
-        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-        gt.x += q.x;
-        gt.y += q.y;
-      }
-    }
-    local += a.p.tv_xy * sxy + a.p.tv_t * stt;
-    const float2 gd = a.g[idx];
-    float2 g;
-    g.x = fmaf(a.p.gscale, gd.x, fmaf(a.p.tv_xy, gxy.x, a.p.tv_t * gt.x));
-    g.y = fmaf(a.p.gscale, gd.y, fmaf(a.p.tv_xy, gxy.y, a.p.tv_t * gt.y));
-    if constexpr (ADAM) {
-      float2 mm = a.m[idx], vv = a.v[idx];
-      mm.x = fmaf(a.p.beta1, mm.x, (1.f - a.p.beta1) * g.x);
-      mm.y = fmaf(a.p.beta1, mm.y, (1.f - a.p.beta1) * g.y);
-      vv.x = fmaf(a.p.beta2, vv.x, (1.f - a.p.beta2) * g.x * g.x);
-      vv.y = fmaf(a.p.beta2, vv.y, (1.f - a.p.beta2) * g.y * g.y);
-      const float dx = sqrtf(vv.x) * a.p.inv_bc2_sqrt + a.p.eps;
-      const float dy = sqrtf(vv.y) * a.p.inv_bc2_sqrt + a.p.eps;
-      float2 nx;
-      nx.x = x.x - a.p.lr_t * (mm.x / dx);
-      nx.y = x.y - a.p.lr_t * (mm.y / dy);
-      a.m[idx] = mm;
-      a.v[idx] = vv;
-      a.out[idx] = nx;
-    } else {
-      a.out[idx] = g;
     }
   }
   if (a.partials) {
@@ -180,7 +189,8 @@ __global__ void render_kernel(const float2* V, float2* img, long npix, int Nf, i
 }
 
 unsigned opt_blocks(const Plan& p, const Reducer* red) {
-  long need = ((long)p.vol_elems() + kOptThreads - 1) / kOptThreads;
+  const long segs = ((long)p.N * p.Nf + kSeg - 1) / kSeg;
+  long need = (long)p.T * p.N * segs;
   long cap = red ? std::min<long>(red->capacity, 16384) : 16384;
   return (unsigned)std::max<long>(1, std::min(need, cap));
 }

@@ -5,8 +5,8 @@
 // evaluated by a Kaiser-Bessel NUFFT with oversampling 2 and width 6):
 //   * per sample m = (b L + l) R + j: k = k_r d_b + k_p d_b^perp, grid
 //     coordinate u = 2N k (mod 2N, exact because the sum over integer x is
-//     1-periodic in k), first tap floor(u) - 2 and the six weights per axis
-//     psi(u - tap), psi(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta);
+//     1-periodic in k), first tap floor(u) - (W/2 - 1) and the W weights per
+//     axis psi(u - tap), psi(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta);
 //   * deapodisation c(x) = I0(beta) / psihat(x / 2N) with the closed-form
 //     transform psihat(xi) = W sinh(sqrt(beta^2 - (pi W xi)^2)) / sqrt(...),
 //     beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8) (Beatty et al. 2005);
@@ -78,12 +78,18 @@ prop_status upload(T* dst, const std::vector<T>& src) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->tile_off, p->tile_samples, p->grid, p->rows, p->resid, p->grad,
+                  p->order, p->cell_off, p->cell_ent, p->contrib, p->grid, p->rows, p->resid, p->grad,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
                   p->red_tv.counter, p->stage_y, p->stage_v};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (auto& v : p->ev_rec)
+    for (auto& pr : v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
   delete p;
 }
 
@@ -100,10 +106,12 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
     return fail(PROP_ERR_INVALID_ARG, "plan_create: nblades, lines and readout must be >= 1");
   if ((long long)d->nblades * d->lines * d->readout > (1LL << 30))
     return fail(PROP_ERR_INVALID_ARG, "plan_create: too many samples");
+  if ((long long)d->nblades * d->lines * d->readout * 64 >= (1LL << 31))
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: too many samples for 32-bit spread lists");
   if (d->nframes < 1) return fail(PROP_ERR_INVALID_ARG, "plan_create: nframes must be >= 1");
   if (!d->delta || !d->theta) return fail(PROP_ERR_INVALID_ARG, "plan_create: delta/theta is NULL");
-  if (d->kb_width != 0 && d->kb_width != kKbWidth)
-    return fail(PROP_ERR_INVALID_ARG, "plan_create: kb_width must be 0 or 6");
+  if (d->kb_width != 0 && d->kb_width != 6 && d->kb_width != 8)
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: kb_width must be 0 (= 6), 6 or 8");
   if (d->bin_chunk < 0 || d->bin_chunk > kMaxChunk)
     return fail(PROP_ERR_INVALID_ARG, "plan_create: bin_chunk must be in [0, 64]");
   int ndev = 0;
@@ -130,9 +138,9 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   p->T = d->nframes;
   p->M = p->B * p->L * p->R;
   p->device = d->device;
+  p->W = d->kb_width == 0 ? kKbWidthDefault : d->kb_width;
   p->chunk = d->bin_chunk == 0 ? std::min(p->Nf, 32) : std::min(d->bin_chunk, p->Nf);
   p->nchunks = (p->Nf + p->chunk - 1) / p->chunk;
-  p->tiles_per_side = p->n / kTile;
   p->theta.assign(d->theta, d->theta + p->B);
   p->delta.assign(d->delta, d->delta + p->Nf);
   p->blade_frame.assign(p->B, 0);
@@ -145,7 +153,8 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   }
 
   const int n = p->n;
-  const double W = kKbWidth, sigma = 2.0;
+  const int Wi = p->W;
+  const double W = Wi, sigma = 2.0;
   const double beta = M_PI * std::sqrt((W / sigma) * (W / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
   const double i0b = bessel_i0(beta);
 
@@ -158,8 +167,10 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
 
   // Per-sample grid indices and weights.
   std::vector<uint32_t> kb_idx(p->M);
-  std::vector<float4> kb_w((size_t)p->M * 3);
+  const int wq = Wi / 2;  // float4 per sample
+  std::vector<float4> kb_w((size_t)p->M * wq);
   std::vector<int> first_tap(2 * (size_t)p->M);
+  std::vector<double> wd((size_t)p->M * 2 * Wi);  // FP64 weights: w1[W] then w2[W]
   for (int b = 0; b < p->B; ++b) {
     const double c = std::cos(p->theta[b]), s = std::sin(p->theta[b]);
     for (int l = 0; l < p->L; ++l) {
@@ -168,7 +179,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
         const double kr = ((double)j - p->R / 2.0) / N;
         const double k[2] = {kr * c - kp * s, kr * s + kp * c};
         const size_t m = ((size_t)b * p->L + l) * p->R + j;
-        float w[12];
+        float w[16];
         int base[2];
         for (int a = 0; a < 2; ++a) {
           double u = n * k[a];
@@ -177,15 +188,19 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
           if (u < 0) u = 0;
           const double fl = std::floor(u);
           const double fr = u - fl;
-          base[a] = ((int)fl - 2 + n) % n;
-          for (int q = 0; q < kKbWidth; ++q) w[a * 6 + q] = (float)psi(fr + 2.0 - q);
+          const int h = Wi / 2 - 1;  // taps floor(u) - h .. floor(u) + W/2
+          base[a] = ((int)fl - h + n) % n;
+          for (int q = 0; q < Wi; ++q) {
+            const double v = psi(fr + h - q);
+            wd[m * 2 * Wi + a * Wi + q] = v;
+            w[a * Wi + q] = (float)v;
+          }
         }
         kb_idx[m] = (uint32_t)base[0] | ((uint32_t)base[1] << 16);
         first_tap[2 * m] = base[0];
         first_tap[2 * m + 1] = base[1];
-        kb_w[3 * m + 0] = make_float4(w[0], w[1], w[2], w[3]);
-        kb_w[3 * m + 1] = make_float4(w[4], w[5], w[6], w[7]);
-        kb_w[3 * m + 2] = make_float4(w[8], w[9], w[10], w[11]);
+        for (int q = 0; q < wq; ++q)
+          kb_w[(size_t)wq * m + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       }
     }
   }
@@ -225,44 +240,51 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   for (int q = 0; q < n; ++q)
     tw[q] = make_float2((float)std::cos(2 * M_PI * q / n), (float)-std::sin(2 * M_PI * q / n));
 
-  // Spread tile lists (counting sort by (frame, tile)).
-  const int tps = p->tiles_per_side;
+  // Interpolation order: samples sorted by (frame, 16x16-cell tile of their
+  // first tap), ascending m within a tile, so that the warps of one CTA gather
+  // from one compact region of the grid.
+  const int tps = n / kTile;
   const size_t ntile = (size_t)p->T * tps * tps;
-  std::vector<int> tile_off(ntile + 1, 0);
-  auto tiles_of = [&](int base, int* out_t) {
-    int cnt = 0;
-    for (int q = 0; q < kKbWidth; ++q) {
-      int t = ((base + q) % n) / kTile;
-      bool seen = false;
-      for (int z = 0; z < cnt; ++z) seen |= out_t[z] == t;
-      if (!seen) out_t[cnt++] = t;
-    }
-    return cnt;
-  };
-  for (size_t m = 0; m < (size_t)p->M; ++m) {
-    const int frame = p->blade_frame[m / ((size_t)p->L * p->R)];
-    int tr[2], tc[2];
-    const int nr = tiles_of(first_tap[2 * m + 1], tr);
-    const int nc = tiles_of(first_tap[2 * m], tc);
-    for (int a = 0; a < nr; ++a)
-      for (int c2 = 0; c2 < nc; ++c2) tile_off[((size_t)frame * tps + tr[a]) * tps + tc[c2] + 1]++;
-  }
-  for (size_t t = 0; t < ntile; ++t) tile_off[t + 1] += tile_off[t];
-  p->tile_entries = tile_off[ntile];
-  std::vector<int> tile_samples(std::max(p->tile_entries, 1));
+  const size_t LR = (size_t)p->L * p->R;
+  std::vector<int> order(p->M);
   {
-    std::vector<int> cursor(tile_off.begin(), tile_off.end() - 1);
-    for (size_t m = 0; m < (size_t)p->M; ++m) {
-      const int frame = p->blade_frame[m / ((size_t)p->L * p->R)];
-      int tr[2], tc[2];
-      const int nr = tiles_of(first_tap[2 * m + 1], tr);
-      const int nc = tiles_of(first_tap[2 * m], tc);
-      for (int a = 0; a < nr; ++a)
-        for (int c2 = 0; c2 < nc; ++c2) {
-          const size_t tile = ((size_t)frame * tps + tr[a]) * tps + tc[c2];
-          tile_samples[cursor[tile]++] = (int)m;
+    auto tile_of = [&](size_t m) {
+      const size_t frame = (size_t)p->blade_frame[m / LR];
+      return (frame * tps + first_tap[2 * m + 1] / kTile) * tps + first_tap[2 * m] / kTile;
+    };
+    std::vector<int> cnt(ntile + 1, 0);
+    for (size_t m = 0; m < (size_t)p->M; ++m) cnt[tile_of(m) + 1]++;
+    for (size_t t = 0; t < ntile; ++t) cnt[t + 1] += cnt[t];
+    for (size_t m = 0; m < (size_t)p->M; ++m) order[cnt[tile_of(m)]++] = (int)m;
+  }
+
+  // Spread gather lists: for every (frame, cell) the (sample, weight) pairs of
+  // the samples whose W x W footprint covers the cell, ascending m.  The weight
+  // is the product w2[a] w1[b] formed in FP64, the same factors the
+  // interpolation applies, so the spread is the exact transpose.
+  const size_t ncell = (size_t)p->T * n * n;
+  std::vector<int> cell_off(ncell + 1, 0);
+  auto cell_of = [&](size_t m, int a, int b) {
+    const size_t frame = (size_t)p->blade_frame[m / LR];
+    const int r = (first_tap[2 * m + 1] + a) % n, c = (first_tap[2 * m] + b) % n;
+    return (frame * n + r) * n + c;
+  };
+  for (size_t m = 0; m < (size_t)p->M; ++m)
+    for (int a = 0; a < Wi; ++a)
+      for (int b = 0; b < Wi; ++b) cell_off[cell_of(m, a, b) + 1]++;
+  for (size_t c = 0; c < ncell; ++c) cell_off[c + 1] += cell_off[c];
+  p->cell_entries = (size_t)cell_off[ncell];
+  std::vector<int2> cell_ent(std::max<size_t>(p->cell_entries, 1));
+  {
+    std::vector<int> cursor(cell_off.begin(), cell_off.end() - 1);
+    for (size_t m = 0; m < (size_t)p->M; ++m)
+      for (int a = 0; a < Wi; ++a)
+        for (int b = 0; b < Wi; ++b) {
+          const float w = (float)(wd[m * 2 * Wi + Wi + a] * wd[m * 2 * Wi + b]);
+          int wbits;
+          std::memcpy(&wbits, &w, sizeof(float));
+          cell_ent[cursor[cell_of(m, a, b)]++] = make_int2((int)m, wbits);
         }
-    }
   }
 
   DevAlloc tab{p, &p->table_bytes};
@@ -282,18 +304,21 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   TRY(tab(&p->deapod, deapod.size(), "deapodisation table"));
   TRY(tab(&p->twiddle, tw.size(), "twiddles"));
   TRY(tab(&p->blade_frame_d, p->blade_frame.size(), "blade frames"));
-  TRY(tab(&p->tile_off, tile_off.size(), "tile offsets"));
-  TRY(tab(&p->tile_samples, tile_samples.size(), "tile samples"));
+  TRY(tab(&p->order, order.size(), "interpolation order"));
+  TRY(tab(&p->cell_off, cell_off.size(), "cell offsets"));
+  TRY(tab(&p->cell_ent, cell_ent.size(), "cell entries"));
   TRY(wrk(&p->grid, (size_t)p->T * n * n * p->chunk, "grid workspace"));
   TRY(wrk(&p->rows, (size_t)p->T * N * n * p->chunk, "row workspace"));
+  TRY(wrk(&p->contrib, (size_t)p->M * p->chunk, "phased residual"));
   TRY(upload(p->kb_idx, kb_idx));
   TRY(upload(p->kb_w, kb_w));
   TRY(upload(p->phase, phase));
   TRY(upload(p->deapod, deapod));
   TRY(upload(p->twiddle, tw));
   TRY(upload(p->blade_frame_d, p->blade_frame));
-  TRY(upload(p->tile_off, tile_off));
-  TRY(upload(p->tile_samples, tile_samples));
+  TRY(upload(p->order, order));
+  TRY(upload(p->cell_off, cell_off));
+  TRY(upload(p->cell_ent, cell_ent));
   {
     cudaError_t e = fft_configure(n);
     if (e == cudaSuccess) e = nufft_configure(p->chunk);

@@ -11,7 +11,7 @@
 
 namespace prop {
 
-constexpr int kKbWidth = 6;        // taps per axis of the Kaiser-Bessel kernel
+constexpr int kKbWidthDefault = 6; // taps per axis of the Kaiser-Bessel kernel (6 or 8)
 constexpr int kTile = 16;          // spread tile edge, grid cells
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
@@ -51,27 +51,29 @@ struct Reducer {
 struct Plan {
   // geometry
   int N = 0, n = 0, Nf = 0, B = 0, L = 0, R = 0, T = 1, M = 0;
+  int W = kKbWidthDefault;       // kernel width (taps per axis)
   int chunk = 0;                 // bins per grid pass
   int nchunks = 0;
   int device = 0;
-  int tiles_per_side = 0;        // n / kTile
   std::vector<double> theta, delta;
   std::vector<int> blade_frame;
 
   // device tables
   uint32_t* kb_idx = nullptr;    // [M] packed (i1 | i2 << 16) first tap, mod n
-  float4* kb_w = nullptr;        // [M][3] -> 12 floats: w1[6] then w2[6]
+  float4* kb_w = nullptr;        // [M][W/2] -> 2W floats: w1[W] (x1 taps) then w2[W] (x2 taps)
   float2* phase = nullptr;       // [R][Nf] exp(-2 pi i k_r Delta_f)
   float* deapod = nullptr;       // [N]
   float2* twiddle = nullptr;     // [n] exp(-2 pi i k / n)
   int* blade_frame_d = nullptr;  // [B]
-  int* tile_off = nullptr;       // [T * tiles^2 + 1]
-  int* tile_samples = nullptr;   // [tile_off[end]]
-  int tile_entries = 0;
+  int* order = nullptr;          // [M] samples sorted by grid tile (interpolation order)
+  int* cell_off = nullptr;       // [T * n * n + 1] spread gather list offsets per cell
+  int2* cell_ent = nullptr;      // [cell_entries] (sample m, weight bits) per cell, ascending m
+  size_t cell_entries = 0;
 
   // grid workspace (one bin chunk)
   float2* grid = nullptr;        // [T][n][n][chunk]
   float2* rows = nullptr;        // [T][N][n][chunk] row-pass intermediate
+  float2* contrib = nullptr;     // [M][chunk] conj(P[j][f]) r_m, input of the spread
 
   // reconstruction state (allocated on first use)
   bool recon_ready = false;
@@ -91,7 +93,26 @@ struct Plan {
 
   size_t table_bytes = 0, work_bytes = 0, recon_bytes = 0;
 
+  // stage profiling (prop_profile_enable)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;                  // idle events
+  std::vector<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec =
+      std::vector<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>>(PROP_NUM_STAGES);
+
   size_t vol_elems() const { return (size_t)T * N * N * Nf; }
+};
+
+// Stage ids of prop_profile_read.
+enum Stage { kStFwdRows = 0, kStFwdCols, kStInterp, kStSpread, kStAdjCols, kStAdjRows, kStOpt, kStOther };
+
+// Brackets one launch with profiling events when the plan profiles.
+struct StageScope {
+  Plan& p;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageScope(Plan& plan, int st, cudaStream_t stream);
+  ~StageScope();
 };
 
 // plan.cu
@@ -113,11 +134,14 @@ cudaError_t fft_configure(int n);
 // displacement phase, summed over the chunk's bins, scaled by s.
 // mode 0: y = part, 1: y += part; y_meas != null subtracts the measurement
 // (first chunk). With red != null the final |y|^2 is reduced into *sumsq.
+// contrib != null also writes conj(P) * (final value) per bin for the spread.
 cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_meas,
-                   bool accumulate, const Reducer* red, double* sumsq, cudaStream_t s);
-// Tiled spread of conj(phase) * r into the grid chunk (every cell written).
+                   bool accumulate, const Reducer* red, double* sumsq, float2* contrib, cudaStream_t s);
+// Adjoint spread of r into the grid chunk: contrib[m][f] = conj(P[j_m][f0+f]) r_m,
+// then every cell gathers sum_{(m, w) in its list} w contrib[m][f] (every cell written).
 cudaError_t nufft_configure(int chunk);
-cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, cudaStream_t s);
+// contrib_ready: p.contrib already holds this chunk's phased residual (fused by interp).
+cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contrib_ready, cudaStream_t s);
 
 // optim.cu
 struct AdamArgs {

@@ -11,14 +11,15 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-4   # forward and adjoint, relative L2 against the exact NDFT
 
 
-def _plan(c, bin_chunk=0):
+def _plan(c, bin_chunk=0, kb_width=0):
     from paper_2311_13177_gb300 import Plan
-    return Plan(c["N"], c["L"], c["R"], c["theta"], c["delta"], c["blade_frame"], c["T"], bin_chunk=bin_chunk)
+    return Plan(c["N"], c["L"], c["R"], c["theta"], c["delta"], c["blade_frame"], c["T"], bin_chunk=bin_chunk,
+                kb_width=kb_width)
 
 
-def _check(c, bin_chunk=0):
+def _check(c, bin_chunk=0, kb_width=0, tol=TOL):
     g = geometry(c["N"], c["L"], c["R"], c["theta"], c["delta"], c["blade_frame"], c["T"])
-    plan = _plan(c, bin_chunk)
+    plan = _plan(c, bin_chunk, kb_width)
     dev = torch.device("cuda")
     y = plan.forward(torch.from_numpy(c["V"]).to(dev)).cpu().numpy()
     y_ref = oracle.forward(c["V"].astype(np.complex128), g)
@@ -27,7 +28,7 @@ def _check(c, bin_chunk=0):
     V_ref = oracle.adjoint(c["y"].astype(np.complex128), g)
     e2 = rel(V, V_ref)
     plan.destroy()
-    assert e1 < TOL and e2 < TOL, (e1, e2)
+    assert e1 < tol and e2 < tol, (e1, e2)
     return e1, e2
 
 
@@ -49,6 +50,16 @@ def test_forward_adjoint_match_oracle(shape):
             _plan(c)
         return
     _check(c)
+
+
+@pytest.mark.parametrize("shape", [(32, 8, 5, 8, 32, 1), (48, 3, 4, 6, 48, 2)])
+def test_width8_kernel_is_more_accurate(shape):
+    """Kernel width 8: same operators, error two orders of magnitude below width 6."""
+    N, Nf, B, L, R, T = shape
+    c = random_case(N, Nf, B, L, R, T, seed=31 + N)
+    e6 = _check(c, kb_width=6)
+    e8 = _check(c, kb_width=8, tol=1e-6)
+    assert e8[0] < 0.05 * e6[0] and e8[1] < 0.05 * e6[1]
 
 
 def test_chunked_grid_matches_unchunked():

@@ -22,13 +22,19 @@ def _params(w, iters):
             oracle.ReconParams(iters=iters, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps))
 
 
-@pytest.mark.parametrize("name,iters", [("tiny", 20), ("dyn_small", 20), ("small64", 100)])
-def test_reconstruction_matches_oracle(name, iters):
+# The small dynamic problem runs at kernel width 8: with width 6 the NUFFT's
+# ~6e-6 operator error is amplified by Adam's sign-like early steps to ~1.6e-3
+# after 20 iterations even in exact arithmetic (an FP64 emulation of the
+# width-6 NUFFT trajectory against the exact-NDFT oracle gives 1.6e-3; width
+# 8 gives 1e-6), so only width 8 tests the temporal path at the 1e-3 bar.
+@pytest.mark.parametrize("name,iters,kbw", [("tiny", 20, 6), ("tiny", 20, 8), ("dyn_small", 20, 8),
+                                            ("small64", 100, 6)])
+def test_reconstruction_matches_oracle(name, iters, kbw):
     from paper_2311_13177_gb300 import Plan
     w, p = workload_case(name)
     g = geometry(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
     pg, po = _params(w, iters)
-    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T, kb_width=kbw)
     V, tr = plan.reconstruct(torch.from_numpy(p["y"]).cuda(), pg)
     Vo, tro = oracle.reconstruct(p["y"].astype(np.complex128), g, po)
     e = rel(V.cpu().numpy(), Vo)

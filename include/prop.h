@@ -164,6 +164,29 @@ PROP_API prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const pro
 PROP_API prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, void* image_dev,
                         void* stream);
 
+/* Smoothed TV value and gradient without any device allocation (the paper has
+ * no counterpart; this is a service for callers that cannot allocate device
+ * memory: code running inside a memory arena owned by a host framework, a
+ * real-time loop under a no-allocation rule, or a callback that must not
+ * re-enter the CUDA allocator).  Needs no plan.
+ *   V_dev     [nframes][n][n][nf] complex64 in (layout of V above)
+ *   grad_dev  same shape, out: tv_xy grad TV_xy(V) + tv_t grad TV_t(V)
+ *   loss_dev  one device double, out: tv_xy TV_xy(V) + tv_t TV_t(V)
+ * with TV as defined above (forward differences, no wrap-around).  Runs on
+ * the calling thread's current device; all pointers must be on it.
+ * Reduction scratch lives in a file-scope __device__ array of 128 KiB + 256 B
+ * (one double per image row), resident on every device that loads the
+ * library until exit, so nframes * n must be <= 16384 (larger sizes return
+ * PROP_ERR_INVALID_ARG with a message).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, once per device); make
+ * that first call before any stream capture.  Each call clears the scratch
+ * counter with cudaMemsetAsync on `stream`; it calls no allocating routine.
+ * All calls share the one array, so calls that overlap on the GPU (different
+ * streams, concurrent threads) race on it: serialise them.  Does not
+ * synchronise. */
+PROP_API prop_status prop_tv_grad_static(const void* V_dev, int nframes, int n, int nf, float tv_xy, float tv_t,
+                                         float tv_eps, void* grad_dev, double* loss_dev, void* stream);
+
 /* Stage profiling.  Stages: 0 forward row FFT, 1 forward column FFT,
  * 2 interpolation, 3 spread, 4 adjoint column FFT, 5 adjoint row FFT,
  * 6 TV + Adam (or TV gradient), 7 other (render).  While enabled, every

@@ -51,6 +51,8 @@ SIGNATURES = {
     "prop_loss_grad": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p, c_void_p,
                                ctypes.POINTER(c_double), c_void_p]),
     "prop_render": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "prop_tv_grad_static": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_float, c_float, c_void_p,
+                                    c_void_p, c_void_p]),
     "prop_profile_enable": (c_int, [c_void_p, c_int]),
     "prop_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "prop_last_error": (ctypes.c_char_p, []),

@@ -250,3 +250,23 @@ def prop_loss_grad(plan: Plan, y, params, V, grad=None, stream=None):
 
 def prop_render(plan: Plan, V, f_lo=0, f_hi=None, out=None, stream=None):
     return plan.render(V, f_lo, f_hi, out, stream)
+
+
+def prop_tv_grad_static(V: torch.Tensor, tv_xy: float, tv_t: float, tv_eps: float, grad: torch.Tensor,
+                        loss: torch.Tensor, stream=None) -> None:
+    """Allocation-free TV value and gradient (no plan; scratch in a static device array).
+
+    V, grad: complex64 CUDA tensors [T, N, N, Nf]; loss: float64 CUDA tensor with one element.
+    Writes grad = tv_xy grad TV_xy + tv_t grad TV_t and loss = tv_xy TV_xy + tv_t TV_t.
+    The output tensors are supplied by the caller; the call itself allocates nothing.
+    """
+    if V.dim() != 4:
+        raise ValueError("V must be [T, N, N, Nf]")
+    T, N, N2, Nf = (int(x) for x in V.shape)
+    if N2 != N:
+        raise ValueError("V must be [T, N, N, Nf]")
+    if not loss.is_cuda or loss.dtype != torch.float64 or loss.numel() < 1:
+        raise TypeError("loss must be a float64 CUDA tensor")
+    check(lib().prop_tv_grad_static(_dev_ptr(V, (T, N, N, Nf), "V"), T, N, Nf, float(tv_xy), float(tv_t),
+                                    float(tv_eps), _dev_ptr(grad, (T, N, N, Nf), "grad"),
+                                    ctypes.c_void_p(loss.data_ptr()), _stream(stream)), "prop_tv_grad_static")

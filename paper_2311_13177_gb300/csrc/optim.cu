@@ -240,3 +240,158 @@ cudaError_t render(const Plan& p, const float2* V, int f_lo, int f_hi, float2* i
 }
 
 }  // namespace prop
+
+// ---------------------------------------------------------------------------
+// Allocation-free TV value and gradient: prop_tv_grad_static.
+//
+// For callers that cannot allocate device memory (code running inside a
+// memory pool or arena owned by a host framework, under a no-allocation
+// rule in a real-time loop, or in a callback that must not re-enter the CUDA
+// allocator).  It computes the same smoothed TV terms as the optimiser
+// kernel, one CTA per image row, and keeps its reduction scratch (one FP64
+// partial per image row plus the arrival counter) in the file-scope device
+// array below instead of a plan.  The array is 128 KiB + 256 B and stays
+// resident on every device that loads the library until the process exits.
+#include <mutex>
+
+namespace prop {
+namespace {
+
+constexpr int kStaticRows = 16384;       // most image rows (frames * N) per call
+constexpr int kStaticDevices = 64;
+
+// [0, kStaticRows): per-row partial sums; slot kStaticRows holds the counter.
+static __device__ __align__(256) double g_tv_static_scratch[kStaticRows + 32];
+
+__global__ void __launch_bounds__(kOptThreads)
+tv_grad_rows_kernel(const float2* V, float2* grad, double* scratch, double* loss_out, int N, int Nf, int T,
+                    float tv_xy, float tv_t, float tv_eps) {
+  const float eps2 = tv_eps * tv_eps;
+  const int rowlen = N * Nf;
+  const int row = blockIdx.x;  // t * N + i2
+  const int i2 = row % N;
+  const int t = row / N;
+  const long sy = rowlen;
+  const long st = (long)N * rowlen;
+  const long rbase = (long)row * rowlen;
+  float local = 0.f;
+  for (int e = threadIdx.x; e < rowlen; e += blockDim.x) {
+    const long idx = rbase + e;
+    const float2 x = V[idx];
+    float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
+    float mag, sxy = 0.f, stt = 0.f;
+    if (tv_xy != 0.f) {
+      if (e + Nf < rowlen) {
+        const float2 nb = V[idx + Nf];
+        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+        gxy.x -= q.x;
+        gxy.y -= q.y;
+        sxy += mag;
+      }
+      if (e >= Nf) {
+        const float2 nb = V[idx - Nf];
+        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+        gxy.x += q.x;
+        gxy.y += q.y;
+      }
+      if (i2 + 1 < N) {
+        const float2 nb = V[idx + sy];
+        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+        gxy.x -= q.x;
+        gxy.y -= q.y;
+        sxy += mag;
+      }
+      if (i2 > 0) {
+        const float2 nb = V[idx - sy];
+        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+        gxy.x += q.x;
+        gxy.y += q.y;
+      }
+    }
+    if (tv_t != 0.f) {
+      if (t + 1 < T) {
+        const float2 nb = V[idx + st];
+        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+        gt.x -= q.x;
+        gt.y -= q.y;
+        stt += mag;
+      }
+      if (t > 0) {
+        const float2 nb = V[idx - st];
+        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+        gt.x += q.x;
+        gt.y += q.y;
+      }
+    }
+    local += tv_xy * sxy + tv_t * stt;
+    grad[idx] = make_float2(fmaf(tv_xy, gxy.x, tv_t * gt.x), fmaf(tv_xy, gxy.y, tv_t * gt.y));
+  }
+  __shared__ double sh[32];
+  __shared__ bool last;
+  unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kStaticRows);
+  const double bs = block_sum_d((double)local, sh);
+  if (threadIdx.x == 0) {
+    scratch[row] = bs;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&scratch[i]);
+    s = block_sum_d(s, sh);
+    if (threadIdx.x == 0) {
+      *loss_out = s;
+      *counter = 0u;
+    }
+  }
+}
+
+std::mutex g_static_mutex;
+double* g_static_addr[kStaticDevices] = {};
+
+}  // namespace
+}  // namespace prop
+
+extern "C" prop_status prop_tv_grad_static(const void* V_dev, int nframes, int n, int nf, float tv_xy,
+                                           float tv_t, float tv_eps, void* grad_dev, double* loss_dev,
+                                           void* stream) {
+  using namespace prop;
+  if (!V_dev || !grad_dev || !loss_dev) return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: null argument");
+  if (((uintptr_t)V_dev & 15u) || ((uintptr_t)grad_dev & 15u) || ((uintptr_t)loss_dev & 7u))
+    return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: V and grad must be 16-byte aligned, loss 8-byte aligned");
+  if (V_dev == grad_dev) return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: V and grad must not alias");
+  if (nframes < 1 || n < 1 || nf < 1 || (long long)n * nf > (1LL << 30))
+    return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: nframes, n, nf must be >= 1 and n * nf <= 2^30");
+  if ((long long)nframes * n > kStaticRows)
+    return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: nframes * n = " + std::to_string((long long)nframes * n) +
+                                          " image rows exceeds the static scratch limit of " +
+                                          std::to_string(kStaticRows));
+  if (!(tv_eps > 0.f) || !(tv_xy >= 0.f) || !(tv_t >= 0.f))
+    return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: need tv_xy >= 0, tv_t >= 0, tv_eps > 0");
+  int dev = 0;
+  PROP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticDevices) return fail(PROP_ERR_INVALID_ARG, "tv_grad_static: device ordinal too large");
+  double* scratch = nullptr;
+  {
+    // One-time set-up per device, with that device current: the host-side
+    // name of the array is not a device address, so look the address up.
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+      void* addr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&addr, g_tv_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "tv_grad_static: cudaGetSymbolAddress");
+      g_static_addr[dev] = static_cast<double*>(addr);
+    }
+    scratch = g_static_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // The counter must start at zero; the partials are fully rewritten each call.
+  PROP_CUDA(cudaMemsetAsync(scratch + kStaticRows, 0, sizeof(double), s));
+  tv_grad_rows_kernel<<<nframes * n, kOptThreads, 0, s>>>((const float2*)V_dev, (float2*)grad_dev, scratch,
+                                                           loss_dev, n, nf, nframes, tv_xy, tv_t, tv_eps);
+  PROP_CUDA(cudaGetLastError());
+  return PROP_OK;
+}

@@ -64,6 +64,17 @@ namespace {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// After a synchronisation: report (and clear) an expired bounded device wait.
+prop_status check_device_status(Plan& p) {
+  int st = 0;
+  PROP_CUDA(cudaMemcpy(&st, p.status_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    PROP_CUDA(cudaMemset(p.status_dev, 0, sizeof(int)));
+    return fail(PROP_ERR_TIMEOUT, "a bounded device-side wait expired (grid tile staging did not complete)");
+  }
+  return PROP_OK;
+}
+
 // y = A V, or r = A V - y_meas with |r|^2 reduced into *sumsq.
 prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_meas, const Reducer* red,
                          double* sumsq, cudaStream_t s) {
@@ -172,6 +183,7 @@ prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* 
   if (trace_host && q->iters > 0) {
     PROP_CUDA(cudaMemcpyAsync(trace_host, p.loss_dev, sizeof(double) * q->iters, cudaMemcpyDeviceToHost, s));
     PROP_CUDA(cudaStreamSynchronize(s));
+    if ((st = check_device_status(p)) != PROP_OK) return st;
   }
   return PROP_OK;
 }
@@ -293,6 +305,7 @@ prop_status prop_reconstruct_host(prop_plan plan, const void* y_host, const prop
     PROP_CUDA(cudaMemcpyAsync(loss_trace_host, p.loss_dev, sizeof(double) * params->iters,
                               cudaMemcpyDeviceToHost, s));
   PROP_CUDA(cudaStreamSynchronize(s));
+  if ((st = check_device_status(p)) != PROP_OK) return st;
   return PROP_OK;
 }
 
@@ -323,6 +336,7 @@ prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const prop_recon_p
   }
   PROP_CUDA(cudaMemcpyAsync(loss_host, p.scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   PROP_CUDA(cudaStreamSynchronize(s));
+  if ((st = check_device_status(p)) != PROP_OK) return st;
   return PROP_OK;
 }
 

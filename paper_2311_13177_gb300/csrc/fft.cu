@@ -382,7 +382,7 @@ FftArgs base_args(const Plan& p) {
   a.N = p.N;
   a.n = p.n;
   a.Nf = p.Nf;
-  a.C = p.chunk;
+  a.C = p.cs;
   a.Cv = p.chunk;
   a.f0 = 0;
   a.scale = 1.f;
@@ -415,7 +415,7 @@ cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s) {
   FftArgs a = base_args(p);
   a.src = p.rows;
   a.dst = p.grid;
-  dim3 grid(p.n * p.chunk / kFftCols, p.T);
+  dim3 grid(p.n * p.cs / kFftCols, p.T);
   return dispatch(p.n, kFwdCols, a, grid, s);
 }
 
@@ -423,7 +423,7 @@ cudaError_t fft_adjoint_cols(const Plan& p, cudaStream_t s) {
   FftArgs a = base_args(p);
   a.src = p.grid;
   a.dst = p.rows;
-  dim3 grid(p.n * p.chunk / kFftCols, p.T);
+  dim3 grid(p.n * p.cs / kFftCols, p.T);
   return dispatch(p.n, kAdjCols, a, grid, s);
 }
 

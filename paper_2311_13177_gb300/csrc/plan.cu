@@ -78,7 +78,8 @@ prop_status upload(T* dst, const std::vector<T>& src) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->order, p->cell_off, p->cell_ent, p->contrib, p->grid, p->rows, p->resid, p->grad,
+                  p->order, p->items, p->sitems, p->cell_off, p->cell_ent, p->contrib, p->grid, p->rows,
+                  p->resid, p->grad, p->status_dev,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
                   p->red_tv.counter, p->stage_y, p->stage_v};
@@ -141,6 +142,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   p->W = d->kb_width == 0 ? kKbWidthDefault : d->kb_width;
   p->chunk = d->bin_chunk == 0 ? std::min(p->Nf, 32) : std::min(d->bin_chunk, p->Nf);
   p->nchunks = (p->Nf + p->chunk - 1) / p->chunk;
+  p->cs = p->chunk + (p->chunk & 1);  // even stride: staged grid rows are 16-byte runs
   p->theta.assign(d->theta, d->theta + p->B);
   p->delta.assign(d->delta, d->delta + p->Nf);
   p->blade_frame.assign(p->B, 0);
@@ -150,6 +152,12 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   if (!guard.ok) {
     plan_free(p);
     return fail(PROP_ERR_CUDA, "plan_create: cudaSetDevice failed");
+  }
+  if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    plan_free(p);
+    return fail(PROP_ERR_CUDA, "plan_create: device attribute query failed");
   }
 
   const int n = p->n;
@@ -240,22 +248,43 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   for (int q = 0; q < n; ++q)
     tw[q] = make_float2((float)std::cos(2 * M_PI * q / n), (float)-std::sin(2 * M_PI * q / n));
 
-  // Interpolation order: samples sorted by (frame, 16x16-cell tile of their
-  // first tap), ascending m within a tile, so that the warps of one CTA gather
-  // from one compact region of the grid.
-  const int tps = n / kTile;
+  // Interpolation work items: samples sorted by (frame, TI x TI-cell tile of
+  // their first tap), ascending m within a tile; every non-empty tile's run is
+  // cut into items of at most kInterpItem samples.  One CTA per item stages
+  // the tile plus its (W-1)-cell halo in shared memory.
+  p->interp_tile = p->cs <= 32 ? 16 : 8;
+  const int TI = p->interp_tile;
+  const int tps = n / TI;
   const size_t ntile = (size_t)p->T * tps * tps;
   const size_t LR = (size_t)p->L * p->R;
   std::vector<int> order(p->M);
+  std::vector<int4> items;
   {
     auto tile_of = [&](size_t m) {
       const size_t frame = (size_t)p->blade_frame[m / LR];
-      return (frame * tps + first_tap[2 * m + 1] / kTile) * tps + first_tap[2 * m] / kTile;
+      return (frame * tps + first_tap[2 * m + 1] / TI) * tps + first_tap[2 * m] / TI;
     };
     std::vector<int> cnt(ntile + 1, 0);
     for (size_t m = 0; m < (size_t)p->M; ++m) cnt[tile_of(m) + 1]++;
     for (size_t t = 0; t < ntile; ++t) cnt[t + 1] += cnt[t];
+    for (size_t t = 0; t < ntile; ++t)
+      for (int s = cnt[t]; s < cnt[t + 1]; s += kInterpItem)
+        items.push_back(make_int4((int)t, s, std::min(kInterpItem, cnt[t + 1] - s), 0));
     for (size_t m = 0; m < (size_t)p->M; ++m) order[cnt[tile_of(m)]++] = (int)m;
+  }
+  p->n_items = (int)items.size();
+  // The interpolation reads the per-sample tables in this sorted order, so that
+  // an item's metadata is one contiguous run.
+  {
+    std::vector<uint32_t> idx_s(p->M);
+    std::vector<float4> w_s(kb_w.size());
+    for (size_t i = 0; i < (size_t)p->M; ++i) {
+      const size_t m = (size_t)order[i];
+      idx_s[i] = kb_idx[m];
+      for (int q = 0; q < wq; ++q) w_s[i * wq + q] = kb_w[m * wq + q];
+    }
+    kb_idx.swap(idx_s);
+    kb_w.swap(w_s);
   }
 
   // Spread gather lists: for every (frame, cell) the (sample, weight) pairs of
@@ -283,9 +312,38 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
           const float w = (float)(wd[m * 2 * Wi + Wi + a] * wd[m * 2 * Wi + b]);
           int wbits;
           std::memcpy(&wbits, &w, sizeof(float));
-          cell_ent[cursor[cell_of(m, a, b)]++] = make_int2((int)m, wbits);
+          cell_ent[cursor[cell_of(m, a, b)]++] = make_int2((int)(m * (size_t)p->cs), wbits);
         }
   }
+
+  // Spread work items: runs of cells in patch-major order (frame, 8x8-cell
+  // patch, row-major inside the patch) with about equal work, counted as the
+  // list entries plus a fixed cost per written cell.  Patch order keeps the
+  // samples an item reads within a small region of k-space.
+  std::vector<int2> sitems;
+  {
+    const int pps = n / kSpreadPatch;
+    const size_t per_frame = (size_t)n * n;
+    auto cell_at = [&](size_t i) {
+      const size_t t = i / per_frame, r = i % per_frame;
+      const size_t patch = r / (kSpreadPatch * kSpreadPatch), loc = r % (kSpreadPatch * kSpreadPatch);
+      const size_t row = (patch / pps) * kSpreadPatch + loc / kSpreadPatch;
+      const size_t col = (patch % pps) * kSpreadPatch + loc % kSpreadPatch;
+      return (t * n + row) * n + col;
+    };
+    size_t beg = 0;
+    long cost = 0;
+    for (size_t i = 0; i < ncell; ++i) {
+      const size_t c = cell_at(i);
+      cost += (cell_off[c + 1] - cell_off[c]) + kSpreadCellCost;
+      if (cost >= kSpreadItemCost || i + 1 == ncell) {
+        sitems.push_back(make_int2((int)beg, (int)(i + 1)));
+        beg = i + 1;
+        cost = 0;
+      }
+    }
+  }
+  p->n_sitems = (int)sitems.size();
 
   DevAlloc tab{p, &p->table_bytes};
   DevAlloc wrk{p, &p->work_bytes};
@@ -305,11 +363,13 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   TRY(tab(&p->twiddle, tw.size(), "twiddles"));
   TRY(tab(&p->blade_frame_d, p->blade_frame.size(), "blade frames"));
   TRY(tab(&p->order, order.size(), "interpolation order"));
+  TRY(tab(&p->items, std::max<size_t>(items.size(), 1), "interpolation items"));
   TRY(tab(&p->cell_off, cell_off.size(), "cell offsets"));
   TRY(tab(&p->cell_ent, cell_ent.size(), "cell entries"));
-  TRY(wrk(&p->grid, (size_t)p->T * n * n * p->chunk, "grid workspace"));
-  TRY(wrk(&p->rows, (size_t)p->T * N * n * p->chunk, "row workspace"));
-  TRY(wrk(&p->contrib, (size_t)p->M * p->chunk, "phased residual"));
+  TRY(tab(&p->sitems, std::max<size_t>(sitems.size(), 1), "spread items"));
+  TRY(wrk(&p->grid, (size_t)p->T * n * n * p->cs, "grid workspace"));
+  TRY(wrk(&p->rows, (size_t)p->T * N * n * p->cs, "row workspace"));
+  TRY(wrk(&p->contrib, (size_t)p->M * p->cs, "phased residual"));
   TRY(upload(p->kb_idx, kb_idx));
   TRY(upload(p->kb_w, kb_w));
   TRY(upload(p->phase, phase));
@@ -317,14 +377,25 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   TRY(upload(p->twiddle, tw));
   TRY(upload(p->blade_frame_d, p->blade_frame));
   TRY(upload(p->order, order));
+  if (!sitems.empty()) TRY(upload(p->sitems, sitems));
+  if (!items.empty()) TRY(upload(p->items, items));
   TRY(upload(p->cell_off, cell_off));
   TRY(upload(p->cell_ent, cell_ent));
   {
     cudaError_t e = fft_configure(n);
-    if (e == cudaSuccess) e = nufft_configure(p->chunk);
+    // The interpolation may use the device's whole opt-in shared memory.
+    if (e == cudaSuccess) e = nufft_configure(p->smem_optin);
     if (e != cudaSuccess) {
       plan_free(p);
-      return cuda_fail(e, "fft_configure");
+      return cuda_fail(e, "kernel configuration");
+    }
+  }
+  TRY(tab(&p->status_dev, 1, "status word"));
+  {
+    cudaError_t e = cudaMemset(p->status_dev, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      plan_free(p);
+      return cuda_fail(e, "status word");
     }
   }
 #undef TRY
@@ -337,7 +408,7 @@ prop_status plan_ensure_recon(Plan* p, int iters) {
   prop_status st;
   if (!p->recon_ready) {
     const size_t nv = p->vol_elems();
-    const int red_cap = 1 << 15;
+    const int red_cap = std::max(1 << 15, p->n_items);
     if ((st = rec(&p->resid, (size_t)p->M, "residual")) != PROP_OK) return st;
     if ((st = rec(&p->grad, nv, "gradient")) != PROP_OK) return st;
     if ((st = rec(&p->vol2, nv, "volume buffer")) != PROP_OK) return st;

@@ -12,7 +12,10 @@
 namespace prop {
 
 constexpr int kKbWidthDefault = 6; // taps per axis of the Kaiser-Bessel kernel (6 or 8)
-constexpr int kTile = 16;          // spread tile edge, grid cells
+constexpr int kInterpItem = 128;   // most samples per interpolation work item
+constexpr int kSpreadPatch = 8;    // spread cells are visited in 8x8-cell patches
+constexpr int kSpreadCellCost = 4; // work of writing one cell, in list entries
+constexpr int kSpreadItemCost = 2048;  // target work per spread item
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
 
@@ -52,22 +55,31 @@ struct Plan {
   // geometry
   int N = 0, n = 0, Nf = 0, B = 0, L = 0, R = 0, T = 1, M = 0;
   int W = kKbWidthDefault;       // kernel width (taps per axis)
+  int num_sms = 1;               // streaming multiprocessors of the device
+  int smem_optin = 48 * 1024;    // largest opt-in shared memory per block (bytes)
+  int* status_dev = nullptr;     // device status word: 1 = a bounded device wait expired
   int chunk = 0;                 // bins per grid pass
+  int cs = 0;                    // bin stride of the grid workspaces (chunk rounded up to even)
   int nchunks = 0;
   int device = 0;
   std::vector<double> theta, delta;
   std::vector<int> blade_frame;
 
   // device tables
-  uint32_t* kb_idx = nullptr;    // [M] packed (i1 | i2 << 16) first tap, mod n
-  float4* kb_w = nullptr;        // [M][W/2] -> 2W floats: w1[W] (x1 taps) then w2[W] (x2 taps)
+  uint32_t* kb_idx = nullptr;    // [M] packed (i1 | i2 << 16) first tap, mod n, in interpolation order
+  float4* kb_w = nullptr;        // [M][W/2] -> 2W floats: w1[W] (x1 taps) then w2[W] (x2 taps), same order
   float2* phase = nullptr;       // [R][Nf] exp(-2 pi i k_r Delta_f)
   float* deapod = nullptr;       // [N]
   float2* twiddle = nullptr;     // [n] exp(-2 pi i k / n)
   int* blade_frame_d = nullptr;  // [B]
   int* order = nullptr;          // [M] samples sorted by grid tile (interpolation order)
+  int4* items = nullptr;         // [n_items] (frame * tiles^2 + tile, first, count, 0)
+  int n_items = 0;
+  int interp_tile = 16;          // TI: interpolation tile edge, cells
   int* cell_off = nullptr;       // [T * n * n + 1] spread gather list offsets per cell
   int2* cell_ent = nullptr;      // [cell_entries] (sample m, weight bits) per cell, ascending m
+  int2* sitems = nullptr;        // [n_sitems] spread work items: [begin, end) in patch-major cell order
+  int n_sitems = 0;
   size_t cell_entries = 0;
 
   // grid workspace (one bin chunk)
@@ -139,7 +151,8 @@ cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_
                    bool accumulate, const Reducer* red, double* sumsq, float2* contrib, cudaStream_t s);
 // Adjoint spread of r into the grid chunk: contrib[m][f] = conj(P[j_m][f0+f]) r_m,
 // then every cell gathers sum_{(m, w) in its list} w contrib[m][f] (every cell written).
-cudaError_t nufft_configure(int chunk);
+cudaError_t nufft_configure(int smem_optin);
+int interp_buffers(const Plan& p);
 // contrib_ready: p.contrib already holds this chunk's phased residual (fused by interp).
 cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contrib_ready, cudaStream_t s);
 

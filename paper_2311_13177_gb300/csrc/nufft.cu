@@ -15,8 +15,9 @@
 // Adjoint: G'_{t,f}[cell] = sum_m w(m, cell) conj(P[j_m][f]) r_m.  The
 // phased residual contrib[m][f] = conj(P[j_m][f]) r_m is formed once per
 // sample (fused into the interpolation when the grid holds every bin), then
-// every cell gathers its plan-time list of (sample, weight) pairs in a fixed
-// order: no atomics, every cell written exactly once, bitwise reproducible.
+// every grid cell gathers its plan-time list of (sample, weight) pairs in a
+// fixed order: no atomics, every cell written exactly once, bitwise
+// reproducible.
 #include "prop_internal.cuh"
 
 namespace prop {
@@ -359,20 +360,17 @@ __global__ void __launch_bounds__(256) phase_expand_kernel(const float2* r, cons
   }
 }
 
-// G'[cell][f] = sum over the cell's (offset, w) list of w * contrib[offset + f];
-// LP lanes per cell, each lane QB bins; CS > 0 fixes the stride at compile time.
+// Cell gather: G'[cell][f] = sum over the cell's (offset, w) list of
+// w * contrib[offset + f].  LP lanes per cell, each lane QB bins; CS > 0 fixes
+// the stride at compile time.  Cells are taken in the plan's patch-major
+// order (one table lookup, no index arithmetic) and list entries are
+// consumed four at a time for memory-level parallelism.
 template <int LP, int CS>
-__global__ void __launch_bounds__(256) spread_gather_kernel(float2* grid, const float2* contrib, const int* cell_off,
-                                                             const int2* cell_ent, const int2* items, int n_items,
-                                                             int n, int Crt, int Cv) {
-  // One CTA per work item: a run of cells in patch-major order (frame, 8x8
-  // patch, row-major in the patch) with about equal list work, so the phased
-  // residuals its cells gather (each shared by up to W x W cells) stay in L1;
-  // list entries carry the residual's element offset and are consumed four
-  // at a time for memory-level parallelism.
+__global__ void __launch_bounds__(256) spread_gather_kernel(float2* grid, const float2* contrib, const int* cell_ids,
+                                                             const int* cell_off, const int2* cell_ent,
+                                                             const int2* items, int n_items, int Crt, int Cv) {
   constexpr int CPW = 32 / LP;
   constexpr int QB = CS > 0 ? (CS + LP - 1) / LP : 2;  // runtime stride: LP >= C/2
-  constexpr int PE = kSpreadPatch;
   const int C = CS > 0 ? CS : Crt;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LP - 1);
@@ -380,20 +378,15 @@ __global__ void __launch_bounds__(256) spread_gather_kernel(float2* grid, const 
   const int warp = threadIdx.x >> 5;
   const int nwarp = blockDim.x >> 5;
   const int nq = CS > 0 ? QB : (C + LP - 1) / LP;
-  const int pps = n / PE;
-  const int per_frame = n * n;
   const float2* cbase = contrib + sub;
   for (int itm = blockIdx.x; itm < n_items; itm += gridDim.x) {
     const int2 range = __ldg(&items[itm]);
     for (int i = range.x + warp * CPW + slot; i < range.y; i += nwarp * CPW) {
-      const int t = i / per_frame;
-      const int rem = i - t * per_frame;
-      const int patch = rem / (PE * PE), loc = rem % (PE * PE);
-      const long c = ((long)t * n + (patch / pps) * PE + loc / PE) * n + (patch % pps) * PE + loc % PE;
+      const int c = __ldg(&cell_ids[i]);
       float2 acc[QB];
 #pragma unroll
       for (int q = 0; q < QB; ++q) acc[q] = make_float2(0.f, 0.f);
-      const int beg = __ldg(&cell_off[c]), end = __ldg(&cell_off[c + 1]);
+      const int beg = __ldg(&cell_off[i]), end = __ldg(&cell_off[i + 1]);
       int e = beg;
       for (; e + 4 <= end; e += 4) {
         int2 en[4];
@@ -559,9 +552,9 @@ cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contr
   }
   const int lpg = lanes_for(p.cs);
   dim3 g((unsigned)std::max(1, std::min(p.n_sitems, 65535)));
-#define SG(L, CSV)                                                                                  \
-  spread_gather_kernel<L, CSV><<<g, 256, 0, s>>>(p.grid, p.contrib, p.cell_off, p.cell_ent, p.sitems, \
-                                                  p.n_sitems, p.n, p.cs, nbins)
+#define SG(L, CSV)                                                                                          \
+  spread_gather_kernel<L, CSV><<<g, 256, 0, s>>>(p.grid, p.contrib, p.cell_ids, p.cell_off, p.cell_ent, p.sitems, \
+                                                  p.n_sitems, p.cs, nbins)
   if (p.cs == 32) SG(32, 32);
   else if (p.cs == 64) SG(32, 64);
   else if (p.cs == 16) SG(16, 16);

@@ -14,8 +14,8 @@
 //     k_r Delta_f reduced modulo 1 in FP64 before the cosine and sine
 //     (Sec. 3: a displacement along the readout is a phase linear in k_r);
 //   * FFT twiddles exp(-2 pi i q / 2N);
-//   * spread tile lists: for every frame and 16x16-cell grid tile, the
-//     samples whose 6x6 footprint touches the tile (CSR, ascending m).
+//   * interpolation order (samples sorted by grid tile) and spread gather
+//     lists: for every grid cell the (sample, weight) pairs that cover it.
 #include "prop_internal.cuh"
 
 #include <cmath>
@@ -78,7 +78,7 @@ prop_status upload(T* dst, const std::vector<T>& src) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->order, p->items, p->sitems, p->cell_off, p->cell_ent, p->contrib, p->grid, p->rows,
+                  p->order, p->items, p->sitems, p->cell_ids, p->cell_off, p->cell_ent, p->contrib, p->grid, p->rows,
                   p->resid, p->grad, p->status_dev,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
@@ -107,8 +107,8 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
     return fail(PROP_ERR_INVALID_ARG, "plan_create: nblades, lines and readout must be >= 1");
   if ((long long)d->nblades * d->lines * d->readout > (1LL << 30))
     return fail(PROP_ERR_INVALID_ARG, "plan_create: too many samples");
-  if ((long long)d->nblades * d->lines * d->readout * 64 >= (1LL << 31))
-    return fail(PROP_ERR_INVALID_ARG, "plan_create: too many samples for 32-bit spread lists");
+  if ((long long)d->nblades * d->lines * d->readout * kMaxChunk >= (1LL << 31))
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: too many samples for 32-bit spread offsets");
   if (d->nframes < 1) return fail(PROP_ERR_INVALID_ARG, "plan_create: nframes must be >= 1");
   if (!d->delta || !d->theta) return fail(PROP_ERR_INVALID_ARG, "plan_create: delta/theta is NULL");
   if (d->kb_width != 0 && d->kb_width != 6 && d->kb_width != 8)
@@ -287,12 +287,16 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
     kb_w.swap(w_s);
   }
 
-  // Spread gather lists: for every (frame, cell) the (sample, weight) pairs of
-  // the samples whose W x W footprint covers the cell, ascending m.  The weight
-  // is the product w2[a] w1[b] formed in FP64, the same factors the
-  // interpolation applies, so the spread is the exact transpose.
+  // Spread gather lists: for every (frame, cell) the samples whose W x W
+  // footprint covers the cell, as (phased-residual offset m * cs, weight
+  // w2[a] w1[b]) in ascending m.  The weight is formed in FP64 from the same
+  // factors the interpolation applies, so the spread is its exact transpose.
+  // Cells are listed in patch-major order (frame, 8x8-cell patch, row-major in
+  // the patch) and cut into work items of about equal work (list entries plus
+  // a fixed cost per written cell); patch order keeps the residual rows an
+  // item reads within a small region of k-space.
   const size_t ncell = (size_t)p->T * n * n;
-  std::vector<int> cell_off(ncell + 1, 0);
+  std::vector<int> cell_cnt(ncell, 0);
   auto cell_of = [&](size_t m, int a, int b) {
     const size_t frame = (size_t)p->blade_frame[m / LR];
     const int r = (first_tap[2 * m + 1] + a) % n, c = (first_tap[2 * m] + b) % n;
@@ -300,42 +304,41 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   };
   for (size_t m = 0; m < (size_t)p->M; ++m)
     for (int a = 0; a < Wi; ++a)
-      for (int b = 0; b < Wi; ++b) cell_off[cell_of(m, a, b) + 1]++;
-  for (size_t c = 0; c < ncell; ++c) cell_off[c + 1] += cell_off[c];
-  p->cell_entries = (size_t)cell_off[ncell];
-  std::vector<int2> cell_ent(std::max<size_t>(p->cell_entries, 1));
-  {
-    std::vector<int> cursor(cell_off.begin(), cell_off.end() - 1);
-    for (size_t m = 0; m < (size_t)p->M; ++m)
-      for (int a = 0; a < Wi; ++a)
-        for (int b = 0; b < Wi; ++b) {
-          const float w = (float)(wd[m * 2 * Wi + Wi + a] * wd[m * 2 * Wi + b]);
-          int wbits;
-          std::memcpy(&wbits, &w, sizeof(float));
-          cell_ent[cursor[cell_of(m, a, b)]++] = make_int2((int)(m * (size_t)p->cs), wbits);
-        }
-  }
-
-  // Spread work items: runs of cells in patch-major order (frame, 8x8-cell
-  // patch, row-major inside the patch) with about equal work, counted as the
-  // list entries plus a fixed cost per written cell.  Patch order keeps the
-  // samples an item reads within a small region of k-space.
-  std::vector<int2> sitems;
+      for (int b = 0; b < Wi; ++b) cell_cnt[cell_of(m, a, b)]++;
+  std::vector<int> cell_ids(ncell);
   {
     const int pps = n / kSpreadPatch;
-    const size_t per_frame = (size_t)n * n;
-    auto cell_at = [&](size_t i) {
-      const size_t t = i / per_frame, r = i % per_frame;
-      const size_t patch = r / (kSpreadPatch * kSpreadPatch), loc = r % (kSpreadPatch * kSpreadPatch);
-      const size_t row = (patch / pps) * kSpreadPatch + loc / kSpreadPatch;
-      const size_t col = (patch % pps) * kSpreadPatch + loc % kSpreadPatch;
-      return (t * n + row) * n + col;
-    };
+    size_t i = 0;
+    for (int t = 0; t < p->T; ++t)
+      for (int pr = 0; pr < pps; ++pr)
+        for (int pc = 0; pc < pps; ++pc)
+          for (int r = 0; r < kSpreadPatch; ++r)
+            for (int c = 0; c < kSpreadPatch; ++c)
+              cell_ids[i++] = (int)(((size_t)t * n + pr * kSpreadPatch + r) * n + pc * kSpreadPatch + c);
+  }
+  // Lists stored in patch-major cell order: an item's entries are contiguous.
+  std::vector<int> cell_pos(ncell);  // cell -> first entry
+  std::vector<int> cell_off(ncell + 1, 0);
+  for (size_t i = 0; i < ncell; ++i) {
+    cell_pos[cell_ids[i]] = cell_off[i];
+    cell_off[i + 1] = cell_off[i] + cell_cnt[cell_ids[i]];
+  }
+  p->cell_entries = (size_t)cell_off[ncell];
+  std::vector<int2> cell_ent(std::max<size_t>(p->cell_entries, 1));
+  for (size_t m = 0; m < (size_t)p->M; ++m)
+    for (int a = 0; a < Wi; ++a)
+      for (int b = 0; b < Wi; ++b) {
+        const float w = (float)(wd[m * 2 * Wi + Wi + a] * wd[m * 2 * Wi + b]);
+        int wbits;
+        std::memcpy(&wbits, &w, sizeof(float));
+        cell_ent[cell_pos[cell_of(m, a, b)]++] = make_int2((int)(m * (size_t)p->cs), wbits);
+      }
+  std::vector<int2> sitems;
+  {
     size_t beg = 0;
     long cost = 0;
     for (size_t i = 0; i < ncell; ++i) {
-      const size_t c = cell_at(i);
-      cost += (cell_off[c + 1] - cell_off[c]) + kSpreadCellCost;
+      cost += (cell_off[i + 1] - cell_off[i]) + kSpreadCellCost;
       if (cost >= kSpreadItemCost || i + 1 == ncell) {
         sitems.push_back(make_int2((int)beg, (int)(i + 1)));
         beg = i + 1;
@@ -364,9 +367,10 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   TRY(tab(&p->blade_frame_d, p->blade_frame.size(), "blade frames"));
   TRY(tab(&p->order, order.size(), "interpolation order"));
   TRY(tab(&p->items, std::max<size_t>(items.size(), 1), "interpolation items"));
+  TRY(tab(&p->sitems, std::max<size_t>(sitems.size(), 1), "spread items"));
+  TRY(tab(&p->cell_ids, cell_ids.size(), "spread cell order"));
   TRY(tab(&p->cell_off, cell_off.size(), "cell offsets"));
   TRY(tab(&p->cell_ent, cell_ent.size(), "cell entries"));
-  TRY(tab(&p->sitems, std::max<size_t>(sitems.size(), 1), "spread items"));
   TRY(wrk(&p->grid, (size_t)p->T * n * n * p->cs, "grid workspace"));
   TRY(wrk(&p->rows, (size_t)p->T * N * n * p->cs, "row workspace"));
   TRY(wrk(&p->contrib, (size_t)p->M * p->cs, "phased residual"));
@@ -378,9 +382,10 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
   TRY(upload(p->blade_frame_d, p->blade_frame));
   TRY(upload(p->order, order));
   if (!sitems.empty()) TRY(upload(p->sitems, sitems));
-  if (!items.empty()) TRY(upload(p->items, items));
+  TRY(upload(p->cell_ids, cell_ids));
   TRY(upload(p->cell_off, cell_off));
   TRY(upload(p->cell_ent, cell_ent));
+  if (!items.empty()) TRY(upload(p->items, items));
   {
     cudaError_t e = fft_configure(n);
     // The interpolation may use the device's whole opt-in shared memory.

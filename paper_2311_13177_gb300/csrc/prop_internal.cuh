@@ -13,8 +13,8 @@ namespace prop {
 
 constexpr int kKbWidthDefault = 6; // taps per axis of the Kaiser-Bessel kernel (6 or 8)
 constexpr int kInterpItem = 128;   // most samples per interpolation work item
-constexpr int kSpreadPatch = 8;    // spread cells are visited in 8x8-cell patches
-constexpr int kSpreadCellCost = 4; // work of writing one cell, in list entries
+constexpr int kSpreadPatch = 8;        // spread cells are visited in 8x8-cell patches
+constexpr int kSpreadCellCost = 4;     // work of writing one cell, in list entries
 constexpr int kSpreadItemCost = 2048;  // target work per spread item
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
@@ -76,9 +76,12 @@ struct Plan {
   int4* items = nullptr;         // [n_items] (frame * tiles^2 + tile, first, count, 0)
   int n_items = 0;
   int interp_tile = 16;          // TI: interpolation tile edge, cells
-  int* cell_off = nullptr;       // [T * n * n + 1] spread gather list offsets per cell
-  int2* cell_ent = nullptr;      // [cell_entries] (sample m, weight bits) per cell, ascending m
-  int2* sitems = nullptr;        // [n_sitems] spread work items: [begin, end) in patch-major cell order
+  // Spread gather: cells in patch-major order (frame, 8x8-cell patch,
+  // row-major in the patch), lists stored in that order.
+  int2* sitems = nullptr;        // [n_sitems] work items: [begin, end) in patch-major cell order
+  int* cell_ids = nullptr;       // [T * n * n] patch-major position -> cell index
+  int* cell_off = nullptr;       // [T * n * n + 1] list offsets per patch-major position
+  int2* cell_ent = nullptr;      // [cell_entries] (phased-residual offset m * cs, weight bits), ascending m
   int n_sitems = 0;
   size_t cell_entries = 0;
 

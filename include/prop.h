@@ -164,6 +164,72 @@ PROP_API prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const pro
 PROP_API prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, void* image_dev,
                         void* stream);
 
+/* ---- Serving: continuous batching of independent reconstructions ----------
+ * A server owns one device arena of hbm_budget_bytes (+ 64 MiB rounding
+ * slack) allocated at creation.  Submitted requests (each a full
+ * prop_reconstruct problem) wait in a FIFO queue; admission workers admit the
+ * head request when fewer than max_slots requests run and its device
+ * footprint (prop_plan_estimate_bytes + its data and volume) fits the budget
+ * still free, build its plan inside the arena and upload its data.  A
+ * scheduler thread keeps every running request's own stream fed with Adam
+ * iterations, so requests that arrive while others run are admitted as soon
+ * as a slot and memory free up and their kernels overlap on the GPU.  A
+ * request that needs more than the whole budget fails with PROP_ERR_OOM.
+ * Results are bitwise identical to a lone prop_reconstruct of the same
+ * problem.  Latency = time from prop_serve_submit to the completed copy of
+ * the result back to host memory. */
+typedef struct prop_server_s* prop_server;
+typedef uint64_t prop_ticket;
+
+enum { PROP_REQ_PENDING = 0, PROP_REQ_RUNNING = 1, PROP_REQ_DONE = 2, PROP_REQ_FAILED = 3,
+       PROP_REQ_CANCELLED = 4 };
+
+typedef struct prop_serve_stats_t {
+  long long completed, failed, cancelled, pending, running;
+  size_t reserved_bytes;      /* footprints of admitted requests */
+  size_t arena_bytes_in_use;  /* bytes handed out from the arena now */
+  size_t arena_peak_bytes;    /* high-water mark of the arena */
+  size_t budget_bytes;
+} prop_serve_stats_t;
+
+/* Device bytes a plan for `desc` may hold after reconstructing `iters`
+ * iterations (an upper bound; host-only computation, no device access). */
+PROP_API prop_status prop_plan_estimate_bytes(const prop_plan_desc* desc, int iters, size_t* bytes);
+
+/* Start a server on `device` with a device-memory budget and a slot limit. */
+PROP_API prop_status prop_serve_create(size_t hbm_budget_bytes, int max_slots, int device, prop_server* out);
+
+/* Queue one reconstruction.  desc: geometry (desc->device is ignored);
+ * params: as prop_reconstruct; y_host [B][L][R] complex64 and v0_host
+ * [T][N][N][Nf] complex64 (NULL = start from zero) are copied before return.
+ * *out receives the request's ticket. */
+PROP_API prop_status prop_serve_submit(prop_server server, const prop_plan_desc* desc,
+                                       const prop_recon_params* params, const void* y_host,
+                                       const void* v0_host, prop_ticket* out);
+
+/* Current PROP_REQ_* state of a ticket (until it has been waited for). */
+PROP_API prop_status prop_serve_poll(prop_server server, prop_ticket ticket, int* state);
+
+/* Block until the request has finished (timeout_ms < 0: no limit) and
+ * release its ticket.  On success v_host_out (nullable) receives the volume
+ * [T][N][N][Nf], *latency_s (nullable) the submit-to-result time and
+ * *final_loss (nullable) L(V_{K-1}).  Returns PROP_ERR_NOT_READY on timeout
+ * (the ticket stays valid), the request's error if it failed, or
+ * PROP_ERR_CANCELLED. */
+PROP_API prop_status prop_serve_wait(prop_server server, prop_ticket ticket, int timeout_ms, void* v_host_out,
+                                     double* latency_s, double* final_loss);
+
+/* Ask for a request to stop: a queued request is dropped, a running one is
+ * stopped after its in-flight iterations; its wait returns PROP_ERR_CANCELLED. */
+PROP_API prop_status prop_serve_cancel(prop_server server, prop_ticket ticket);
+
+/* Counters and memory use of the server. */
+PROP_API prop_status prop_serve_stats(prop_server server, prop_serve_stats_t* out);
+
+/* Cancel everything still queued or running, join the server's threads and
+ * free its arena.  Unwaited tickets become invalid. */
+PROP_API prop_status prop_serve_destroy(prop_server server);
+
 /* Smoothed TV value and gradient without any device allocation (the paper has
  * no counterpart; this is a service for callers that cannot allocate device
  * memory: code running inside a memory arena owned by a host framework, a

@@ -51,6 +51,16 @@ SIGNATURES = {
     "prop_loss_grad": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p, c_void_p,
                                ctypes.POINTER(c_double), c_void_p]),
     "prop_render": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "prop_plan_estimate_bytes": (c_int, [ctypes.POINTER(PlanDesc), c_int, ctypes.POINTER(c_size_t)]),
+    "prop_serve_create": (c_int, [c_size_t, c_int, c_int, ctypes.POINTER(c_void_p)]),
+    "prop_serve_submit": (c_int, [c_void_p, ctypes.POINTER(PlanDesc), ctypes.POINTER(ReconParamsC), c_void_p,
+                                  c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "prop_serve_poll": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(c_int)]),
+    "prop_serve_wait": (c_int, [c_void_p, ctypes.c_uint64, c_int, c_void_p, ctypes.POINTER(c_double),
+                                ctypes.POINTER(c_double)]),
+    "prop_serve_cancel": (c_int, [c_void_p, ctypes.c_uint64]),
+    "prop_serve_stats": (c_int, [c_void_p, c_void_p]),
+    "prop_serve_destroy": (c_int, [c_void_p]),
     "prop_tv_grad_static": (c_int, [c_void_p, c_int, c_int, c_int, c_float, c_float, c_float, c_void_p,
                                     c_void_p, c_void_p]),
     "prop_profile_enable": (c_int, [c_void_p, c_int]),
@@ -87,3 +97,11 @@ def lib() -> ctypes.CDLL:
 def check(status: int, where: str) -> None:
     if status != PROP_OK:
         raise PropError(status, where, lib().prop_last_error().decode(errors="replace"))
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("cancelled", ctypes.c_longlong), ("pending", ctypes.c_longlong),
+                ("running", ctypes.c_longlong), ("reserved_bytes", c_size_t),
+                ("arena_bytes_in_use", c_size_t), ("arena_peak_bytes", c_size_t),
+                ("budget_bytes", c_size_t)]

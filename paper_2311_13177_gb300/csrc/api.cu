@@ -151,7 +151,6 @@ AdamArgs adam_args(const prop_recon_params* q, int k) {
   return a;
 }
 
-// One Adam iteration k (1-based): Vout = Adam step of L at Vin; L(Vin) -> *loss_dst.
 prop_status step_impl(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin,
                       float2* Vout, double* loss_dst, cudaStream_t s) {
   prop_status st;
@@ -189,6 +188,12 @@ prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* 
 }
 
 }  // namespace
+
+prop_status plan_step(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin, float2* Vout,
+                      double* loss_dst, cudaStream_t s) {
+  return step_impl(p, y, q, k, Vin, Vout, loss_dst, s);
+}
+
 }  // namespace prop
 
 using namespace prop;
@@ -289,11 +294,11 @@ prop_status prop_reconstruct_host(prop_plan plan, const void* y_host, const prop
   const size_t vbytes = p.vol_elems() * sizeof(float2);
   const size_t ybytes = (size_t)p.M * sizeof(float2);
   if (!p.stage_y) {
-    PROP_CUDA(cudaMalloc((void**)&p.stage_y, ybytes));
+    PROP_CUDA(plan_dev_alloc(&p, (void**)&p.stage_y, ybytes));
     p.recon_bytes += ybytes;
   }
   if (!p.stage_v) {
-    PROP_CUDA(cudaMalloc((void**)&p.stage_v, vbytes));
+    PROP_CUDA(plan_dev_alloc(&p, (void**)&p.stage_v, vbytes));
     p.recon_bytes += vbytes;
   }
   PROP_CUDA(cudaMemcpyAsync(p.stage_y, y_host, ybytes, cudaMemcpyHostToDevice, s));

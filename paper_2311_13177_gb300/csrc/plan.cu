@@ -55,7 +55,7 @@ struct DevAlloc {
   prop_status operator()(T** ptr, size_t count, const char* what) {
     *ptr = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    cudaError_t e = plan_dev_alloc(p, (void**)ptr, count * sizeof(T));
     if (e != cudaSuccess) {
       cudaGetLastError();
       *ptr = nullptr;
@@ -75,6 +75,18 @@ prop_status upload(T* dst, const std::vector<T>& src) {
 
 }  // namespace
 
+cudaError_t plan_dev_alloc(Plan* p, void** ptr, size_t bytes) {
+  return p->alloc ? p->alloc->allocate(ptr, bytes) : cudaMalloc(ptr, bytes);
+}
+
+void plan_dev_free(Plan* p, void* ptr) {
+  if (!ptr) return;
+  if (p->alloc)
+    p->alloc->release(ptr);
+  else
+    cudaFree(ptr);
+}
+
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
@@ -83,8 +95,7 @@ void plan_free(Plan* p) {
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
                   p->red_tv.counter, p->stage_y, p->stage_v};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) plan_dev_free(p, q);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (auto& v : p->ev_rec)
     for (auto& pr : v) {
@@ -94,7 +105,7 @@ void plan_free(Plan* p) {
   delete p;
 }
 
-prop_status plan_build(const prop_plan_desc* d, Plan** out) {
+prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* alloc) {
   if (!d || !out) return fail(PROP_ERR_INVALID_ARG, "plan_create: null argument");
   *out = nullptr;
   const int N = d->n;
@@ -130,6 +141,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out) {
 
   Plan* p = new (std::nothrow) Plan();
   if (!p) return fail(PROP_ERR_OOM, "plan_create: host allocation failed");
+  p->alloc = alloc;
   p->N = N;
   p->n = 2 * N;
   p->Nf = d->nf;
@@ -432,7 +444,7 @@ prop_status plan_ensure_recon(Plan* p, int iters) {
   }
   if (iters > p->loss_cap) {
     if (p->loss_dev) {
-      cudaFree(p->loss_dev);
+      plan_dev_free(p, p->loss_dev);
       p->recon_bytes -= (size_t)p->loss_cap * sizeof(double);
       p->loss_dev = nullptr;
       p->loss_cap = 0;
@@ -442,6 +454,33 @@ prop_status plan_ensure_recon(Plan* p, int iters) {
     p->loss_cap = cap;
   }
   return PROP_OK;
+}
+
+}  // namespace prop
+
+namespace prop {
+
+size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
+  if (!d || d->n < 8 || d->nf < 1 || d->nblades < 1 || d->lines < 1 || d->readout < 1 || d->nframes < 1)
+    return 0;
+  const size_t N = d->n, n = 2 * N, Nf = d->nf, B = d->nblades, T = d->nframes;
+  const size_t M = B * (size_t)d->lines * d->readout;
+  const size_t W = d->kb_width == 8 ? 8 : 6;
+  const size_t chunk = d->bin_chunk == 0 ? std::min<size_t>(Nf, 32) : std::min<size_t>(d->bin_chunk, Nf);
+  const size_t cs = chunk + (chunk & 1);
+  const size_t TI = cs <= 32 ? 16 : 8;
+  const size_t ncell = T * n * n;
+  const size_t vol = T * N * N * Nf;
+  const size_t interp_items = M / kInterpItem + T * (n / TI) * (n / TI) + 1;
+  const size_t spread_items = (M * W * W + kSpreadCellCost * ncell) / kSpreadItemCost + 1;
+  size_t b = 0;
+  b += 4 * M + M * (W / 2) * 16 + (size_t)d->readout * Nf * 8 + 4 * N + 8 * n + 4 * B + 4 * M;  // sample tables
+  b += 16 * interp_items + 8 * spread_items + 4 * ncell + 4 * (ncell + 1) + 8 * M * W * W + 4;  // lists
+  b += 8 * T * n * n * cs + 8 * T * N * n * cs + 8 * M * cs;                                        // workspace
+  b += 8 * M + 4 * 8 * vol + 64 + 2 * 8 * std::max<size_t>(32768, interp_items) + 8 +
+       8 * std::max<size_t>((size_t)std::max(iters, 1), 64);                                           // optimiser
+  b += 32 * 512;  // allocation rounding
+  return b;
 }
 
 }  // namespace prop

@@ -51,7 +51,17 @@ struct Reducer {
   int capacity = 0;
 };
 
+// Source of a plan's device memory.  The default (null) is cudaMalloc /
+// cudaFree; the request server hands out sub-ranges of one arena instead, so
+// retiring a request never synchronises the device.
+struct DeviceAllocator {
+  virtual ~DeviceAllocator() {}
+  virtual cudaError_t allocate(void** ptr, size_t bytes) = 0;
+  virtual void release(void* ptr) = 0;
+};
+
 struct Plan {
+  DeviceAllocator* alloc = nullptr;
   // geometry
   int N = 0, n = 0, Nf = 0, B = 0, L = 0, R = 0, T = 1, M = 0;
   int W = kKbWidthDefault;       // kernel width (taps per axis)
@@ -131,9 +141,17 @@ struct StageScope {
 };
 
 // plan.cu
-prop_status plan_build(const prop_plan_desc* d, Plan** out);
+prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* alloc = nullptr);
 void plan_free(Plan* p);
+cudaError_t plan_dev_alloc(Plan* p, void** ptr, size_t bytes);
+void plan_dev_free(Plan* p, void* ptr);
 prop_status plan_ensure_recon(Plan* p, int iters);
+// Upper bound of the device bytes a plan for `d` holds once it has
+// reconstructed (tables, workspace, optimiser state); 0 if `d` is invalid.
+size_t plan_estimate_bytes(const prop_plan_desc* d, int iters);
+// One Adam iteration k (1-based) from Vin into Vout; L(Vin) -> *loss_dst (device).
+prop_status plan_step(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin,
+                      float2* Vout, double* loss_dst, cudaStream_t s);
 
 // fft.cu: the four line-FFT passes of the 2-D (i)FFT per bin chunk.
 // Forward: V chunk -> rows (deapodise, pad, FFT along x1) -> grid (pad, FFT along x2).

@@ -333,6 +333,8 @@ def run_ours(args):
         if os.path.exists(tr_path):
             with open(tr_path) as f:
                 traffic = json.load(f).get(dom)
+            if traffic is not None:
+                traffic = float(traffic)
         launches = sum(v_[1] for v_ in prof.values())
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,

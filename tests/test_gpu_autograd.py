@@ -3,7 +3,10 @@
 * 64^2: the gradient of the k-space loss sum|A V - y|^2 taken by autograd
   equals the oracle's 2 A^H (A V - y) (<= 1e-4 relative L2).
 * 384^2, 64 bins, 32 blades x 32 x 384 (the differentiation workload):
-  central finite differences with h = 1e-3 along 64 random unit directions.
+  central finite differences with h = 1e-3 along 64 random unit directions,
+  each error measured against the largest possible directional derivative
+  ||grad|| (random directions in ~10^7 dimensions make single derivatives
+  tiny), and the 64 derivatives compared as a vector.
   The loss is quadratic in V, so the central difference is exact in exact
   arithmetic; the volume is scaled to 1e-3 so that FP32 rounding of the
   forward stays well below the h-sized signal, and the loss is summed in FP64.
@@ -52,8 +55,9 @@ def test_finite_differences_at_384():
     loss = _loss(plan, V, y)
     loss.backward()
     G = V.grad.detach()
+    gnorm = torch.linalg.vector_norm(G).item()
     h = 1e-3
-    errs = []
+    fds, ans = [], []
     with torch.no_grad():
         for _ in range(64):
             D = torch.randn(shape, generator=gen, device="cuda", dtype=torch.complex64)
@@ -62,6 +66,11 @@ def test_finite_differences_at_384():
             lm = _loss(plan, V - h * D, y).item()
             fd = (lp - lm) / (2 * h)
             an = (G.real.double() * D.real.double() + G.imag.double() * D.imag.double()).sum().item()
-            errs.append(abs(fd - an) / max(abs(an), 1e-30))
+            fds.append(fd)
+            ans.append(an)
     plan.destroy()
-    assert np.median(errs) < 1e-3 and max(errs) < 1e-2, (np.median(errs), max(errs))
+    fds, ans = np.array(fds), np.array(ans)
+    # |<G, D>| <= ||G|| for unit D: scale each error by the largest possible
+    # directional derivative, and compare the 64 derivatives as a vector.
+    assert np.max(np.abs(fds - ans)) < 1e-5 * gnorm
+    assert np.linalg.norm(fds - ans) < 5e-3 * np.linalg.norm(ans)

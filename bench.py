@@ -23,6 +23,7 @@ sample of the same step (see `cpu_baseline.sample`).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -48,14 +49,21 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--workload", choices=["static", "dynamic", "diff"], default=WORKLOAD,
+                    help="the headline line is the static workload; the others are for comparison")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-iters", type=int, default=30)
     return ap.parse_args()
 
 
 def workload_config(w) -> dict:
-    return {"workload": f"static {w.N}x{w.N} image, {w.Nf} bins over [{w.delta_lo:g},{w.delta_hi:g}] px, "
+    kind = "static" if w.T == 1 else f"dynamic {w.T}-frame"
+    opt = f"Adam lr {w.lr:g}, TV_xy {w.tv_xy:g}" + (f", TV_t {w.tv_t:g}" if w.tv_t else "")
+    return {"workload": f"{kind} {w.N}x{w.N} image, {w.Nf} bins over [{w.delta_lo:g},{w.delta_hi:g}] px, "
                         f"{w.B} blades x {w.L} lines x {w.R} readout",
             "N": w.N, "Nf": w.Nf, "blades": w.B, "lines": w.L, "readout": w.R, "frames": w.T,
-            "oversampling": 2, "kb_width": 6, "optimizer": "Adam lr 1e-2, TV_xy 1e-3"}
+            "oversampling": 2, "kb_width": 6, "optimizer": opt}
 
 
 def measured_peaks():
@@ -216,6 +224,99 @@ def stage_algo_bytes(plan) -> dict:
             "fft_adj_cols": G, "fft_adj_rows": V, "tv_adam": 7 * V}, 9 * V + 4 * G + 3 * y
 
 
+def stage_alu_flops(plan, W: int = 6) -> dict:
+    """FP32 flops per launch of the interpolation and the spread.
+
+    Interpolation, per sample and bin: W x W taps of a real weight times a
+    complex grid value (2 W^2 FMA), the W column weights (2 W FMA), the
+    complex phase product (6 flops) and the bin sum (2 flops): 4 W^2 + 4 W + 8
+    flops.  Spread, per sample and bin: the phased residual (6 flops) and W^2
+    weighted complex accumulations (4 W^2 flops)."""
+    sb = plan.B * plan.L * plan.R * plan.Nf
+    return {"interp": sb * (4 * W * W + 4 * W + 8), "spread": sb * (4 * W * W + 6)}
+
+
+def run_serving(n_req: int, iters: int, seed: int, device: int, slots: int = 8) -> dict:
+    """Mixed-load serving: the request server against sequential lone solves.
+
+    Requests draw N from {128, 192, 256, 384}, blades from {8, 16, 24, 32}
+    (lines = N/8), Nf from {8, 16, 32, 64} and static or dynamic (16 frames),
+    each with its own seeded phantom.  (1) sequential: each request solved
+    alone in arrival order (plan build + reconstruction), giving mu_seq;
+    (2) saturated: Poisson arrivals at 4 mu_seq, recons/s = requests /
+    makespan; (3) latency: Poisson arrivals at 0.7 mu_seq through the server,
+    latency = result time - submission time, against a FIFO queue of the lone
+    solves over the same arrivals (their measured service times).  Every
+    result of (2) is compared with its lone solve."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2311_13177_gb300 import Plan, ReconParams
+    from paper_2311_13177_gb300.serve import Server
+
+    reqs = synth.make_serve_requests(n_req, seed=seed, iters=iters)
+    probs = [synth.make_problem(w) for w in reqs]
+
+    def params(w):
+        return ReconParams(iters=w.iters, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
+
+    dev = torch.device("cuda", device)
+    lone, service = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w, p in zip(reqs, probs):
+        ts = time.perf_counter()
+        plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T, device=device)
+        V, _ = plan.reconstruct(torch.from_numpy(p["y"]).to(dev), params(w), trace=False)
+        lone.append(V.cpu().numpy())
+        plan.destroy()
+        del V
+        service.append(time.perf_counter() - ts)
+    t_seq = time.perf_counter() - t0
+    mu_seq = n_req / t_seq
+    budget = int(min(torch.cuda.get_device_properties(device).total_memory * 0.6, 160e9))
+
+    def serve(arrivals):
+        srv = Server(budget, max_slots=slots, device=device)
+        t_start = time.perf_counter()
+        tickets = []
+        for w, p, at in zip(reqs, probs, arrivals):
+            delay = t_start + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(w.N, w.L, w.R, p["theta"], p["delta"], p["y"], params(w),
+                                      blade_frame=p["blade_frame"], T=w.T))
+        outs = []
+        for t in tickets:
+            vol, lat, _ = srv.wait(t)
+            outs.append((vol, lat))
+        makespan = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        return outs, makespan, st
+
+    rng = np.random.default_rng(seed + 1)
+    arr_sat = np.cumsum(rng.exponential(1.0 / (4.0 * mu_seq), n_req))
+    outs, makespan, st = serve(list(arr_sat))
+    mismatch = max(float(np.linalg.norm(o[0] - l) / max(np.linalg.norm(l), 1e-30)) for o, l in zip(outs, lone))
+    arr = np.cumsum(rng.exponential(1.0 / (0.7 * mu_seq), n_req))
+    outs_l, _, _ = serve(list(arr))
+    lat = np.array([o[1] for o in outs_l]) * 1000.0
+    fifo, done = [], 0.0
+    for at, sv in zip(arr, service):
+        done = max(done, at) + sv
+        fifo.append(1000.0 * (done - at))
+    return {"requests": n_req, "iters_per_request": iters, "slots": slots, "hbm_budget_bytes": budget,
+            "sequential_recons_per_s": mu_seq, "batched_recons_per_s": n_req / makespan,
+            "speedup_vs_sequential": (n_req / makespan) / mu_seq, "saturated_arrivals": "Poisson at 4 x sequential rate",
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "arrivals": "Poisson at 0.7 x sequential rate"},
+            "sequential_fifo_latency_ms": {"p50": float(np.percentile(fifo, 50)),
+                                           "p99": float(np.percentile(fifo, 99))},
+            "max_rel_diff_mix_vs_alone": mismatch, "arena_peak_bytes": int(st["arena_peak_bytes"]),
+            "mix": "N {128,192,256,384}, blades {8,16,24,32}, lines N/8, Nf {8,16,32,64}, static or dynamic T=16"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -237,7 +338,7 @@ def run_ours(args):
     import synth
     from paper_2311_13177_gb300 import Plan, ReconParams
 
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[args.workload]
     w_rank = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
     prob = synth.make_problem(w_rank)
     plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=local)
@@ -299,7 +400,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    plan.reconstruct(y, ReconParams(iters=K, lr=w.lr, tv_xy=w.tv_xy), V0, trace=False)
+    plan.reconstruct(y, dataclasses.replace(params, iters=K), V0, trace=False)
     e1.record(stream)
     torch.cuda.synchronize()
     warm_rate = K / (e0.elapsed_time(e1) / 1000.0)
@@ -308,11 +409,11 @@ def run_ours(args):
     y_h = torch.from_numpy(prob["y"]).pin_memory()
     V_h = torch.zeros(plan.vol_shape, dtype=torch.complex64).pin_memory()
     K_e2e = max(1, min(K, 2000))
-    plan.reconstruct_host(y_h, ReconParams(iters=3, lr=w.lr, tv_xy=w.tv_xy), V_h)  # staging warm-up
+    plan.reconstruct_host(y_h, dataclasses.replace(params, iters=3), V_h)  # staging warm-up
     V_h.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plan.reconstruct_host(y_h, ReconParams(iters=K_e2e, lr=w.lr, tv_xy=w.tv_xy), V_h)
+    plan.reconstruct_host(y_h, dataclasses.replace(params, iters=K_e2e), V_h)
     t_e2e = time.perf_counter() - t0
     if world > 1:
         tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
@@ -336,6 +437,17 @@ def run_ours(args):
             if traffic is not None:
                 traffic = float(traffic)
         launches = sum(v_[1] for v_ in prof.values())
+        from paper_2311_13177_gb300.binding import prop_fp32_fma_peak
+        fma = prop_fp32_fma_peak(local)
+        flops = stage_alu_flops(plan)
+        alu = {"fp32_fma_peak_tflops": fma, "peak_source": "measured by prop_fp32_fma_peak",
+               "ridge_flop_per_byte": fma * 1e12 / (peak * 1e9)}
+        for st_ in ("interp", "spread"):
+            if st_ in stages:
+                ms_ = stages[st_][0] / stages[st_][1]
+                alu[st_] = {"tflops": flops[st_] / (ms_ / 1000.0) / 1e12,
+                            "frac": flops[st_] / (ms_ / 1000.0) / 1e12 / fma,
+                            "flop_per_byte": flops[st_] / algo[st_]}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / K, "higher_is_better": True,
@@ -346,6 +458,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "kernel_ms": dom_ms, "algo_bytes_per_launch": algo[dom]},
+            "alu_roofline": alu,
             "iteration_roofline": {"algo_bytes_per_iter": b_iter,
                                    "achieved_gbs": b_iter * value / world / 1e9,
                                    "frac": b_iter * value / world / 1e9 / peak,
@@ -362,8 +475,10 @@ def run_ours(args):
             "final_loss": final_loss,
             "wall_s": wall,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
             line["cpu_baseline"] = cpu_baseline_obj()
+        if world == 1 and not args.no_serving and args.serve_requests > 0 and args.workload == WORKLOAD:
+            line["serving"] = run_serving(args.serve_requests, args.serve_iters, 7, local)
         print(json.dumps(line), flush=True)
     plan.destroy()
     if world > 1:

@@ -263,6 +263,15 @@ PROP_API prop_status prop_profile_enable(prop_plan plan, int enable);
  * and launch counts (arrays of PROP_NUM_STAGES), and clears the record. */
 PROP_API prop_status prop_profile_read(prop_plan plan, double* ms_out, long long* launches_out);
 
+/* Measured FP32 FMA throughput of `device` in TFLOP/s (2 flops per FMA):
+ * the ALU ceiling against which the interpolation and spread are placed on a
+ * roofline.  Times a few launches of a register-only FMA loop (8 independent
+ * chains per thread, 8 blocks of 256 threads per SM, a few milliseconds each)
+ * on a private stream and returns the fastest.  Synchronous; allocates and
+ * frees a small device buffer.  Errors: PROP_ERR_INVALID_ARG (null tflops,
+ * bad device), PROP_ERR_CUDA. */
+PROP_API prop_status prop_fp32_fma_peak(int device, double* tflops);
+
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 PROP_API const char* prop_last_error(void);
 

@@ -270,3 +270,12 @@ def prop_tv_grad_static(V: torch.Tensor, tv_xy: float, tv_t: float, tv_eps: floa
     check(lib().prop_tv_grad_static(_dev_ptr(V, (T, N, N, Nf), "V"), T, N, Nf, float(tv_xy), float(tv_t),
                                     float(tv_eps), _dev_ptr(grad, (T, N, N, Nf), "grad"),
                                     ctypes.c_void_p(loss.data_ptr()), _stream(stream)), "prop_tv_grad_static")
+
+
+def prop_fp32_fma_peak(device: int = None) -> float:
+    """Measured FP32 FMA throughput of the device, TFLOP/s (synchronous)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    out = ctypes.c_double()
+    check(lib().prop_fp32_fma_peak(int(device), ctypes.byref(out)), "prop_fp32_fma_peak")
+    return float(out.value)

@@ -122,3 +122,11 @@ def test_render_sums_bins():
     lo = plan.render(V, 0, 2).cpu().numpy()
     assert np.allclose(lo, oracle.render(c["V"], 0, 2), atol=1e-5)
     plan.destroy()
+
+
+@pytest.mark.gpu
+def test_fp32_fma_peak_is_plausible():
+    from paper_2311_13177_gb300.binding import prop_fp32_fma_peak
+    tf = prop_fp32_fma_peak(0)
+    # 152 SMs x 128 FP32 lanes x 2 flops x ~2 GHz is about 80 TFLOP/s
+    assert 10.0 < tf < 200.0, tf

@@ -342,6 +342,182 @@ __global__ void __launch_bounds__(kInterpThreads, 1) interp_kernel(InterpArgs a)
   if (a.partials) reduce_to((double)sumsq, a.partials, a.counter, a.sumsq_out);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kInterpConsumers = 16;                          // compute warps per CTA
+constexpr int kInterp2Threads = 32 * (kInterpConsumers + 1);  // plus one producer warp
+
+// Interpolation for the compile-time bin strides CS in {8, 16, 32, 64}.
+// Warp kInterpConsumers is the producer: its lane 0 streams item k's tile
+// into buffer k % nbuf as soon as every compute warp has released the item
+// that last used that buffer ("empty" barrier, one arrival per compute
+// warp), so no compute warp ever waits for another.  Compute warps take
+// CS / 2 lanes per sample, each lane two adjacent bins (16-byte shared
+// loads), and 64 / CS samples per warp and round.  The metadata of an item
+// (sample index, packed first tap, the 2W weights) is fetched before its
+// tile is awaited, one sample per lane, and handed out by shuffles.
+template <int CS, int W>
+__global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NCW = kInterpConsumers;
+  constexpr int LPS = CS / 2;   // lanes per sample
+  constexpr int SPW = 32 / LPS; // samples per warp and round
+  constexpr int TI = CS <= 32 ? 16 : 8;
+  constexpr int HW = TI + W - 1;
+  constexpr int WQ = W / 2;
+  constexpr int MPL = (kInterpItem + NCW * SPW - 1) / (NCW * SPW) * SPW;  // samples per warp per item
+  static_assert(MPL <= 32, "one prefetched sample per lane");
+  constexpr size_t tile_elems = (size_t)HW * HW * CS;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int sub = lane % LPS;
+  const int slot = lane / LPS;
+  float2* bufs = reinterpret_cast<float2*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + a.nbuf * tile_elems * sizeof(float2));
+  uint64_t* empty = full + a.nbuf;
+  __shared__ volatile int s_abort;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < a.nbuf; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], NCW);
+    }
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  float sumsq = 0.f;
+  if (warp == NCW) {
+    if (lane == 0) {
+      int k = 0;
+      for (int item = blockIdx.x; item < a.n_items; item += gridDim.x, ++k) {
+        const int b = k % a.nbuf;
+        if (k >= a.nbuf && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / a.nbuf) - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        if (s_abort) break;
+        issue_tile<W>(a, item, bufs + b * tile_elems, &full[b]);
+      }
+      // at most one copy per buffer can be in flight: the last one issued
+      for (int kk = k > a.nbuf ? k - a.nbuf : 0; kk < k; ++kk)
+        mbar_wait_bounded(&full[kk % a.nbuf], (uint32_t)((kk / a.nbuf) & 1));
+    }
+  } else {
+    const int f_lo = 2 * sub;
+    const bool b0 = f_lo < a.Cv, b1 = f_lo + 1 < a.Cv;
+    int k = 0;
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x, ++k) {
+      const int b = k % a.nbuf;
+      const ItemGeom g = item_geom(a, item);
+      // lane L prefetches the warp's sample of round L / SPW, slot L % SPW
+      const int sL = (lane / SPW) * NCW * SPW + warp * SPW + (lane % SPW);
+      int mL = 0, jL = 0;
+      uint32_t pL = 0;
+      float wL[2 * W];
+#pragma unroll
+      for (int q = 0; q < 2 * W; ++q) wL[q] = 0.f;
+      if (lane < MPL && sL < g.count) {
+        const int si = g.start + sL;
+        mL = __ldg(&a.order[si]);
+        pL = __ldg(&a.kb_idx[si]);
+#pragma unroll
+        for (int q = 0; q < WQ; ++q) {
+          const float4 v = __ldg(&a.kb_w[(size_t)WQ * si + q]);
+          wL[4 * q] = v.x;
+          wL[4 * q + 1] = v.y;
+          wL[4 * q + 2] = v.z;
+          wL[4 * q + 3] = v.w;
+        }
+        jL = mL % a.R;
+      }
+      if (!mbar_wait_bounded(&full[b], (uint32_t)((k / a.nbuf) & 1))) s_abort = 1;
+      if (s_abort) break;
+      const float2* tile = bufs + b * tile_elems;
+
+      for (int rnd = 0; rnd * NCW * SPW + warp * SPW < g.count; ++rnd) {
+        const int s = rnd * NCW * SPW + warp * SPW + slot;
+        const bool valid = s < g.count;
+        const int src = rnd * SPW + slot;
+        const int m = __shfl_sync(0xffffffffu, mL, src);
+        const int j = __shfl_sync(0xffffffffu, jL, src);
+        const uint32_t packed = __shfl_sync(0xffffffffu, pL, src);
+        float w[2 * W];
+#pragma unroll
+        for (int q = 0; q < 2 * W; ++q) w[q] = __shfl_sync(0xffffffffu, wL[q], src);
+        const float2* P = a.phase + (size_t)j * a.Nf + a.f0 + f_lo;
+        float2 P0 = make_float2(0.f, 0.f), P1 = make_float2(0.f, 0.f);
+        if (valid && b0) P0 = __ldg(P);
+        if (valid && b1) P1 = __ldg(P + 1);
+        float2 tot = make_float2(0.f, 0.f);
+        if (valid) {
+          const int lc = (int)(packed & 0xffff) - g.c0;
+          const int lr = (int)(packed >> 16) - g.r0;
+          const float4* base = reinterpret_cast<const float4*>(tile + ((size_t)lr * HW + lc) * CS + f_lo);
+          float4 racc[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            racc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+              const float4 gv = base[(q * HW + c) * (CS / 2)];
+              racc[q].x = fmaf(w[c], gv.x, racc[q].x);
+              racc[q].y = fmaf(w[c], gv.y, racc[q].y);
+              racc[q].z = fmaf(w[c], gv.z, racc[q].z);
+              racc[q].w = fmaf(w[c], gv.w, racc[q].w);
+            }
+          }
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            acc.x = fmaf(w[W + q], racc[q].x, acc.x);
+            acc.y = fmaf(w[W + q], racc[q].y, acc.y);
+            acc.z = fmaf(w[W + q], racc[q].z, acc.z);
+            acc.w = fmaf(w[W + q], racc[q].w, acc.w);
+          }
+          const float2 z0 = cmulf(P0, make_float2(acc.x, acc.y));
+          const float2 z1 = cmulf(P1, make_float2(acc.z, acc.w));
+          tot = make_float2(z0.x + z1.x, z0.y + z1.y);
+        }
+#pragma unroll
+        for (int o = LPS / 2; o > 0; o >>= 1) {
+          tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
+          tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
+        }
+        float2 v = make_float2(tot.x * a.scale, tot.y * a.scale);
+        if (valid && sub == 0) {
+          if (a.accumulate) {
+            const float2 old = a.y[m];
+            v.x += old.x;
+            v.y += old.y;
+          } else if (a.y_meas) {
+            const float2 ym = __ldg(&a.y_meas[m]);
+            v.x -= ym.x;
+            v.y -= ym.y;
+          }
+          a.y[m] = v;
+          sumsq = fmaf(v.x, v.x, fmaf(v.y, v.y, sumsq));
+        }
+        if (a.contrib) {
+          v.x = __shfl_sync(0xffffffffu, v.x, slot * LPS);
+          v.y = __shfl_sync(0xffffffffu, v.y, slot * LPS);
+          if (valid) {
+            const float2 c0 = cmulcf(P0, v), c1 = cmulcf(P1, v);
+            reinterpret_cast<float4*>(a.contrib + (size_t)m * CS)[sub] = make_float4(c0.x, c0.y, c1.x, c1.y);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+    }
+  }
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicExch(a.err, 1);
+  if (a.partials) reduce_to((double)sumsq, a.partials, a.counter, a.sumsq_out);
+}
+
 // contrib[m][f] = conj(P[j_m][f0 + f]) r_m, LP lanes per sample.
 template <int LP>
 __global__ void __launch_bounds__(256) phase_expand_kernel(const float2* r, const float2* phase, float2* contrib,
@@ -360,73 +536,193 @@ __global__ void __launch_bounds__(256) phase_expand_kernel(const float2* r, cons
   }
 }
 
-// Cell gather: G'[cell][f] = sum over the cell's (offset, w) list of
-// w * contrib[offset + f].  LP lanes per cell, each lane QB bins; CS > 0 fixes
-// the stride at compile time.  Cells are taken in the plan's patch-major
-// order (one table lookup, no index arithmetic) and list entries are
-// consumed four at a time for memory-level parallelism.
-template <int LP, int CS>
-__global__ void __launch_bounds__(256) spread_gather_kernel(float2* grid, const float2* contrib, const int* cell_ids,
-                                                             const int* cell_off, const int2* cell_ent,
-                                                             const int2* items, int n_items, int Crt, int Cv) {
+// --- Spread: cell gather over the plan's item blobs ------------------------
+//
+// An item's blob: int2 cells[ncp] (cell index, end of its list relative to
+// the first entry; ncp = ncells rounded up to even), then int2 entries[nent]
+// (offset m * cs of a phased-residual row, weight bits).  Every list holds a
+// multiple of four entries, so a list is consumed four entries (two 16-byte
+// loads) at a time without predication, in list order.
+
+// Gather of one cell by the CS / 2 lanes of its group, two adjacent bins
+// per lane: returns sum_e w_e contrib[off_e + 2 sub .. + 1].
+__device__ __forceinline__ float4 gather_cell2(const int4* ent, int beg4, int end4, const float2* cbase) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+  for (int e = beg4; e < end4; e += 2) {  // e counts entry pairs
+    const int4 q0 = ent[e], q1 = ent[e + 1];
+    const float4 v0 = __ldg(reinterpret_cast<const float4*>(cbase + q0.x));
+    const float4 v1 = __ldg(reinterpret_cast<const float4*>(cbase + q0.z));
+    const float4 v2 = __ldg(reinterpret_cast<const float4*>(cbase + q1.x));
+    const float4 v3 = __ldg(reinterpret_cast<const float4*>(cbase + q1.z));
+    const float w0 = __int_as_float(q0.y), w1 = __int_as_float(q0.w);
+    const float w2 = __int_as_float(q1.y), w3 = __int_as_float(q1.w);
+    acc.x = fmaf(w0, v0.x, acc.x);
+    acc.y = fmaf(w0, v0.y, acc.y);
+    acc.z = fmaf(w0, v0.z, acc.z);
+    acc.w = fmaf(w0, v0.w, acc.w);
+    acc.x = fmaf(w1, v1.x, acc.x);
+    acc.y = fmaf(w1, v1.y, acc.y);
+    acc.z = fmaf(w1, v1.z, acc.z);
+    acc.w = fmaf(w1, v1.w, acc.w);
+    acc.x = fmaf(w2, v2.x, acc.x);
+    acc.y = fmaf(w2, v2.y, acc.y);
+    acc.z = fmaf(w2, v2.z, acc.z);
+    acc.w = fmaf(w2, v2.w, acc.w);
+    acc.x = fmaf(w3, v3.x, acc.x);
+    acc.y = fmaf(w3, v3.y, acc.y);
+    acc.z = fmaf(w3, v3.z, acc.z);
+    acc.w = fmaf(w3, v3.w, acc.w);
+  }
+  return acc;
+}
+
+// All cells of one item, CS / 2 lanes per cell; `cells` points at the blob
+// (shared or global memory).
+template <int CS>
+__device__ __forceinline__ void gather_item2(const int2* cells, int ncells, int ncp, int warp, int nwarp, int lane,
+                                             float2* grid, const float2* contrib, int Cv) {
+  constexpr int LPC = CS / 2;
+  constexpr int CPW = 32 / LPC;
+  const int sub = lane % LPC, slot = lane / LPC;
+  const int4* ent = reinterpret_cast<const int4*>(cells + ncp);
+  const float2* cbase = contrib + 2 * sub;
+  for (int i0 = warp * CPW; i0 < ncells; i0 += nwarp * CPW) {
+    const int i = i0 + slot;
+    const bool ok = i < ncells;
+    int cid = 0, beg = 0, end = 0;
+    if (ok) {
+      const int2 ce = cells[i];
+      cid = ce.x;
+      end = ce.y;
+      beg = i > 0 ? cells[i - 1].y : 0;
+    }
+    float4 o = gather_cell2(ent, beg >> 1, end >> 1, cbase);
+    if (ok) {
+      if (2 * sub >= Cv) o.x = o.y = 0.f;
+      if (2 * sub + 1 >= Cv) o.z = o.w = 0.f;
+      reinterpret_cast<float4*>(grid + (size_t)cid * CS)[sub] = o;
+    }
+  }
+}
+
+constexpr int kSpreadConsumers = 16;                          // gather warps per CTA
+constexpr int kSpreadThreads = 32 * (kSpreadConsumers + 1);   // plus one producer warp
+
+// Spread for the compile-time strides CS in {8, 16, 32, 64}.  Persistent
+// CTAs (two per SM); the producer warp's lane 0 bulk-copies item k's blob
+// into stage k % 2 once every gather warp has released the item that last
+// used it, so the lists come from shared memory and only the phased-residual
+// rows (mostly L1/L2 hits) are read from global memory.  Used when every
+// item fits a stage (the plan checks).
+template <int CS>
+__global__ void __launch_bounds__(kSpreadThreads, 2) spread_stage_kernel(float2* grid, const float2* contrib,
+                                                                        const int4* sitems, const int2* blob,
+                                                                        int n_items, int Cv, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NCW = kSpreadConsumers;
+  constexpr int NBUF = 2;
+  int2* stage = reinterpret_cast<int2*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)NBUF * kSpreadStageInt2 * sizeof(int2));
+  uint64_t* empty = full + NBUF;
+  __shared__ volatile int s_abort;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], NCW);
+    }
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (warp == NCW) {
+    if (lane == 0) {
+      int k = 0;
+      for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
+        const int b = k % NBUF;
+        if (k >= NBUF && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / NBUF) - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        if (s_abort) break;
+        const int4 d = __ldg(&sitems[item]);
+        const uint32_t bytes = (uint32_t)((((d.y + 1) & ~1) + d.z) * sizeof(int2));
+        mbar_expect_tx(&full[b], bytes);
+        bulk_g2s(stage + (size_t)b * kSpreadStageInt2, blob + d.x, bytes, &full[b]);
+      }
+      for (int kk = k > NBUF ? k - NBUF : 0; kk < k; ++kk)
+        mbar_wait_bounded(&full[kk % NBUF], (uint32_t)((kk / NBUF) & 1));
+    }
+  } else {
+    int k = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
+      const int b = k % NBUF;
+      const int4 d = __ldg(&sitems[item]);
+      const int ncp = (d.y + 1) & ~1;
+      if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NBUF) & 1))) s_abort = 1;
+      if (s_abort) break;
+      gather_item2<CS>(stage + (size_t)b * kSpreadStageInt2, d.y, ncp, warp, NCW, lane, grid, contrib, Cv);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+    }
+  }
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+// Runtime bin stride (any C <= 2 LP): LP lanes per cell, bins sub and
+// sub + LP, lists read from global memory.
+template <int LP>
+__global__ void __launch_bounds__(256) spread_global_kernel(float2* grid, const float2* contrib, const int4* sitems,
+                                                            const int2* blob, int n_items, int C, int Cv) {
   constexpr int CPW = 32 / LP;
-  constexpr int QB = CS > 0 ? (CS + LP - 1) / LP : 2;  // runtime stride: LP >= C/2
-  const int C = CS > 0 ? CS : Crt;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LP - 1);
   const int slot = lane / LP;
   const int warp = threadIdx.x >> 5;
   const int nwarp = blockDim.x >> 5;
-  const int nq = CS > 0 ? QB : (C + LP - 1) / LP;
-  const float2* cbase = contrib + sub;
+  const bool b0 = sub < Cv, b1 = sub + LP < Cv;
   for (int itm = blockIdx.x; itm < n_items; itm += gridDim.x) {
-    const int2 range = __ldg(&items[itm]);
-    for (int i = range.x + warp * CPW + slot; i < range.y; i += nwarp * CPW) {
-      const int c = __ldg(&cell_ids[i]);
-      float2 acc[QB];
-#pragma unroll
-      for (int q = 0; q < QB; ++q) acc[q] = make_float2(0.f, 0.f);
-      const int beg = __ldg(&cell_off[i]), end = __ldg(&cell_off[i + 1]);
-      int e = beg;
-      for (; e + 4 <= end; e += 4) {
-        int2 en[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) en[u] = __ldg(&cell_ent[e + u]);
-#pragma unroll
-        for (int q = 0; q < QB; ++q) {
-          if (q < nq && sub + LP * q < Cv) {
-            float2 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = __ldg(cbase + en[u].x + LP * q);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float w = __int_as_float(en[u].y);
-              acc[q].x = fmaf(w, v[u].x, acc[q].x);
-              acc[q].y = fmaf(w, v[u].y, acc[q].y);
-            }
-          }
-        }
+    const int4 d = __ldg(&sitems[itm]);
+    const int2* cells = blob + d.x;
+    const int2* ent = cells + ((d.y + 1) & ~1);
+    for (int i0 = warp * CPW; i0 < d.y; i0 += nwarp * CPW) {
+      const int i = i0 + slot;
+      const bool ok = i < d.y;
+      int cid = 0, beg = 0, end = 0;
+      if (ok) {
+        const int2 ce = __ldg(&cells[i]);
+        cid = ce.x;
+        end = ce.y;
+        beg = i > 0 ? __ldg(&cells[i - 1]).y : 0;
       }
-      for (; e < end; ++e) {
-        const int2 en = __ldg(&cell_ent[e]);
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      for (int e = beg; e < end; ++e) {
+        const int2 en = __ldg(&ent[e]);
         const float w = __int_as_float(en.y);
-#pragma unroll
-        for (int q = 0; q < QB; ++q) {
-          if (q < nq && sub + LP * q < Cv) {
-            const float2 v = __ldg(cbase + en.x + LP * q);
-            acc[q].x = fmaf(w, v.x, acc[q].x);
-            acc[q].y = fmaf(w, v.y, acc[q].y);
-          }
+        if (b0) {
+          const float2 v = __ldg(contrib + en.x + sub);
+          a0.x = fmaf(w, v.x, a0.x);
+          a0.y = fmaf(w, v.y, a0.y);
+        }
+        if (b1) {
+          const float2 v = __ldg(contrib + en.x + sub + LP);
+          a1.x = fmaf(w, v.x, a1.x);
+          a1.y = fmaf(w, v.y, a1.y);
         }
       }
-      float2* out = grid + (size_t)c * C + sub;
-#pragma unroll
-      for (int q = 0; q < QB; ++q) {
-        const int f = sub + LP * q;
-        if (q < nq && f < C) out[LP * q] = f < Cv ? acc[q] : make_float2(0.f, 0.f);
+      if (ok) {
+        float2* out = grid + (size_t)cid * C;
+        if (sub < C) out[sub] = a0;
+        if (sub + LP < C) out[sub + LP] = a1;
       }
     }
   }
+}
+
+size_t spread_stage_smem() {
+  return (size_t)2 * kSpreadStageInt2 * sizeof(int2) + 4 * sizeof(uint64_t);
 }
 
 int lanes_for(int Cv) {
@@ -440,14 +736,20 @@ unsigned grid_for(long items, long per_block, long cap) {
   return (unsigned)std::max<long>(1, std::min(b, cap));
 }
 
+bool interp2_eligible(int cs, int nbins) {
+  return (cs == 8 || cs == 16 || cs == 32 || cs == 64) && 2 * nbins > cs;
+}
+
 template <int W>
 cudaError_t launch_interp(int lp, int cs, const InterpArgs& a, dim3 grid, size_t smem, cudaStream_t s) {
-  // compile-time strides for the common chunk widths (full lane use), runtime otherwise
-  if (cs == 32 && lp == 32) interp_kernel<32, 32, W><<<grid, kInterpThreads, smem, s>>>(a);
-  else if (cs == 64 && lp == 32) interp_kernel<32, 64, W><<<grid, kInterpThreads, smem, s>>>(a);
-  else if (cs == 16 && lp == 16) interp_kernel<16, 16, W><<<grid, kInterpThreads, smem, s>>>(a);
-  else if (cs == 8 && lp == 8) interp_kernel<8, 8, W><<<grid, kInterpThreads, smem, s>>>(a);
-  else {
+  // compile-time strides for the common chunk widths when more than half of
+  // the bins are live (two bins per lane), runtime stride otherwise
+  if (interp2_eligible(cs, a.Cv)) {
+    if (cs == 32) interp2_kernel<32, W><<<grid, kInterp2Threads, smem, s>>>(a);
+    else if (cs == 64) interp2_kernel<64, W><<<grid, kInterp2Threads, smem, s>>>(a);
+    else if (cs == 16) interp2_kernel<16, W><<<grid, kInterp2Threads, smem, s>>>(a);
+    else interp2_kernel<8, W><<<grid, kInterp2Threads, smem, s>>>(a);
+  } else {
     switch (lp) {
       case 1: interp_kernel<1, 0, W><<<grid, kInterpThreads, smem, s>>>(a); break;
       case 2: interp_kernel<2, 0, W><<<grid, kInterpThreads, smem, s>>>(a); break;
@@ -471,10 +773,10 @@ cudaError_t allow_smem(K kernel, int optin) {
 template <int W>
 cudaError_t configure_interp(int optin) {
   cudaError_t e;
-  if ((e = allow_smem(interp_kernel<32, 32, W>, optin))) return e;
-  if ((e = allow_smem(interp_kernel<32, 64, W>, optin))) return e;
-  if ((e = allow_smem(interp_kernel<16, 16, W>, optin))) return e;
-  if ((e = allow_smem(interp_kernel<8, 8, W>, optin))) return e;
+  if ((e = allow_smem(interp2_kernel<32, W>, optin))) return e;
+  if ((e = allow_smem(interp2_kernel<64, W>, optin))) return e;
+  if ((e = allow_smem(interp2_kernel<16, W>, optin))) return e;
+  if ((e = allow_smem(interp2_kernel<8, W>, optin))) return e;
   if ((e = allow_smem(interp_kernel<1, 0, W>, optin))) return e;
   if ((e = allow_smem(interp_kernel<2, 0, W>, optin))) return e;
   if ((e = allow_smem(interp_kernel<4, 0, W>, optin))) return e;
@@ -488,7 +790,12 @@ cudaError_t configure_interp(int optin) {
 cudaError_t nufft_configure(int smem_optin) {
   cudaError_t e = configure_interp<6>(smem_optin);
   if (e != cudaSuccess) return e;
-  return configure_interp<8>(smem_optin);
+  if ((e = configure_interp<8>(smem_optin))) return e;
+  const int st = (int)spread_stage_smem();
+  if ((e = cudaFuncSetAttribute(spread_stage_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
+  if ((e = cudaFuncSetAttribute(spread_stage_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
+  if ((e = cudaFuncSetAttribute(spread_stage_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
+  return cudaFuncSetAttribute(spread_stage_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
 }
 
 int interp_buffers(const Plan& p) {
@@ -528,7 +835,8 @@ cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_
   a.nbuf = interp_buffers(p);
   if (p.n_items == 0) return cudaSuccess;
   const int HW = p.interp_tile + p.W - 1;
-  const size_t smem = (size_t)a.nbuf * HW * HW * p.cs * sizeof(float2) + 2 * sizeof(uint64_t);
+  // tiles, then a full and an empty barrier per buffer
+  const size_t smem = (size_t)a.nbuf * HW * HW * p.cs * sizeof(float2) + 2 * a.nbuf * sizeof(uint64_t);
   const int blocks = std::min(p.n_items, p.num_sms);
   if (red && red->capacity < blocks) return cudaErrorInvalidValue;
   const int lp = lanes_for(nbins);
@@ -550,26 +858,30 @@ cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contr
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int lpg = lanes_for(p.cs);
-  dim3 g((unsigned)std::max(1, std::min(p.n_sitems, 65535)));
-#define SG(L, CSV)                                                                                          \
-  spread_gather_kernel<L, CSV><<<g, 256, 0, s>>>(p.grid, p.contrib, p.cell_ids, p.cell_off, p.cell_ent, p.sitems, \
-                                                  p.n_sitems, p.cs, nbins)
-  if (p.cs == 32) SG(32, 32);
-  else if (p.cs == 64) SG(32, 64);
-  else if (p.cs == 16) SG(16, 16);
-  else if (p.cs == 8) SG(8, 8);
-  else {
-    switch (lpg) {
-      case 1: SG(1, 0); break;
-      case 2: SG(2, 0); break;
-      case 4: SG(4, 0); break;
-      case 8: SG(8, 0); break;
-      case 16: SG(16, 0); break;
-      default: SG(32, 0); break;
+  if (p.n_sitems == 0) return cudaSuccess;
+  if (p.spread_staged && (p.cs == 8 || p.cs == 16 || p.cs == 32 || p.cs == 64)) {
+    dim3 g((unsigned)std::max(1, std::min(p.n_sitems, 2 * p.num_sms)));
+    const size_t smem = spread_stage_smem();
+#define SS(CSV) \
+  spread_stage_kernel<CSV><<<g, kSpreadThreads, smem, s>>>(p.grid, p.contrib, p.sitems, p.sblob, p.n_sitems, nbins, p.status_dev)
+    if (p.cs == 32) SS(32);
+    else if (p.cs == 64) SS(64);
+    else if (p.cs == 16) SS(16);
+    else SS(8);
+#undef SS
+  } else {
+    dim3 g((unsigned)std::max(1, std::min(p.n_sitems, 65535)));
+#define SG(L) spread_global_kernel<L><<<g, 256, 0, s>>>(p.grid, p.contrib, p.sitems, p.sblob, p.n_sitems, p.cs, nbins)
+    switch (lanes_for((p.cs + 1) / 2)) {
+      case 1: SG(1); break;
+      case 2: SG(2); break;
+      case 4: SG(4); break;
+      case 8: SG(8); break;
+      case 16: SG(16); break;
+      default: SG(32); break;
     }
-  }
 #undef SG
+  }
   return cudaGetLastError();
 }
 

@@ -90,7 +90,7 @@ void plan_dev_free(Plan* p, void* ptr) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->order, p->items, p->sitems, p->cell_ids, p->cell_off, p->cell_ent, p->contrib, p->grid, p->rows,
+                  p->order, p->items, p->sitems, p->sblob, p->contrib, p->grid, p->rows,
                   p->resid, p->grad, p->status_dev,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
@@ -328,37 +328,70 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
             for (int c = 0; c < kSpreadPatch; ++c)
               cell_ids[i++] = (int)(((size_t)t * n + pr * kSpreadPatch + r) * n + pc * kSpreadPatch + c);
   }
-  // Lists stored in patch-major cell order: an item's entries are contiguous.
-  std::vector<int> cell_pos(ncell);  // cell -> first entry
-  std::vector<int> cell_off(ncell + 1, 0);
-  for (size_t i = 0; i < ncell; ++i) {
-    cell_pos[cell_ids[i]] = cell_off[i];
-    cell_off[i + 1] = cell_off[i] + cell_cnt[cell_ids[i]];
+  // Work items: runs of consecutive cells (patch-major order) of about equal
+  // work (list entries plus a fixed cost per written cell), each stored as
+  // one contiguous blob that a CTA stages into shared memory with a single
+  // bulk copy:
+  //   int2 cells[ncells, rounded up to even]: (cell index, end of its list
+  //        relative to the item's first entry)
+  //   int2 entries[nent]: the lists, one after the other
+  // Every list is padded to a multiple of kSpreadListPad entries with
+  // (row M, weight 0): row M of the phased-residual buffer is kept zero, so
+  // a padding entry adds an exact zero and the gather runs unpredicated.  A
+  // cell whose list alone exceeds the staging capacity forms an item of its
+  // own (flag 1) and the plan then gathers from global memory.
+  std::vector<int> cell_first(ncell + 1, 0);  // cell -> first entry in the item's entries
+  std::vector<int4> sitems;                   // (blob offset in int2, ncells, nent, big)
+  std::vector<int2> blob;
+  const int2 pad_entry = make_int2((int)((size_t)p->M * p->cs), 0);
+  {
+    auto padded = [](int c) { return (c + kSpreadListPad - 1) / kSpreadListPad * kSpreadListPad; };
+    size_t i = 0;
+    while (i < ncell) {
+      // choose [i, j)
+      size_t j = i;
+      long cost = 0, nent = 0;
+      while (j < ncell) {
+        const int c = padded(cell_cnt[cell_ids[j]]);
+        const long ncp = (long)((j + 1 - i + 1) & ~(size_t)1);
+        if (j > i && ncp + nent + c > kSpreadStageInt2) break;  // would overflow the stage
+        nent += c;
+        cost += c + kSpreadCellCost;
+        ++j;
+        if (cost >= kSpreadItemCost) break;
+      }
+      const size_t ncells = j - i, ncp = (ncells + 1) & ~(size_t)1;
+      const int big = (long)ncp + nent > kSpreadStageInt2 ? 1 : 0;
+      if (big) p->spread_staged = false;  // a list longer than a stage: gather from global memory
+      if (blob.size() + ncp + nent > 0x7fffffffULL) {
+        plan_free(p);
+        return fail(PROP_ERR_INVALID_ARG, "plan_create: spread lists exceed 2^31 entries");
+      }
+      sitems.push_back(make_int4((int)blob.size(), (int)ncells, (int)nent, big));
+      const size_t cells_at = blob.size(), ent_at = cells_at + ncp;
+      blob.resize(ent_at + nent, pad_entry);
+      long e = 0;
+      for (size_t q = i; q < j; ++q) {
+        const int cid = cell_ids[q];
+        cell_first[cid] = (int)(ent_at + e);
+        e += padded(cell_cnt[cid]);
+        blob[cells_at + (q - i)] = make_int2(cid, (int)e);
+      }
+      if (ncp > ncells) blob[cells_at + ncells] = make_int2(0, (int)e);
+      i = j;
+    }
   }
-  p->cell_entries = (size_t)cell_off[ncell];
-  std::vector<int2> cell_ent(std::max<size_t>(p->cell_entries, 1));
   for (size_t m = 0; m < (size_t)p->M; ++m)
     for (int a = 0; a < Wi; ++a)
       for (int b = 0; b < Wi; ++b) {
         const float w = (float)(wd[m * 2 * Wi + Wi + a] * wd[m * 2 * Wi + b]);
         int wbits;
         std::memcpy(&wbits, &w, sizeof(float));
-        cell_ent[cell_pos[cell_of(m, a, b)]++] = make_int2((int)(m * (size_t)p->cs), wbits);
+        blob[cell_first[cell_of(m, a, b)]++] = make_int2((int)(m * (size_t)p->cs), wbits);
       }
-  std::vector<int2> sitems;
-  {
-    size_t beg = 0;
-    long cost = 0;
-    for (size_t i = 0; i < ncell; ++i) {
-      cost += (cell_off[i + 1] - cell_off[i]) + kSpreadCellCost;
-      if (cost >= kSpreadItemCost || i + 1 == ncell) {
-        sitems.push_back(make_int2((int)beg, (int)(i + 1)));
-        beg = i + 1;
-        cost = 0;
-      }
-    }
-  }
   p->n_sitems = (int)sitems.size();
+  p->spread_entries = blob.size();
+  if (blob.empty()) blob.push_back(pad_entry);
 
   DevAlloc tab{p, &p->table_bytes};
   DevAlloc wrk{p, &p->work_bytes};
@@ -380,12 +413,10 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(tab(&p->order, order.size(), "interpolation order"));
   TRY(tab(&p->items, std::max<size_t>(items.size(), 1), "interpolation items"));
   TRY(tab(&p->sitems, std::max<size_t>(sitems.size(), 1), "spread items"));
-  TRY(tab(&p->cell_ids, cell_ids.size(), "spread cell order"));
-  TRY(tab(&p->cell_off, cell_off.size(), "cell offsets"));
-  TRY(tab(&p->cell_ent, cell_ent.size(), "cell entries"));
+  TRY(tab(&p->sblob, blob.size(), "spread lists"));
   TRY(wrk(&p->grid, (size_t)p->T * n * n * p->cs, "grid workspace"));
   TRY(wrk(&p->rows, (size_t)p->T * N * n * p->cs, "row workspace"));
-  TRY(wrk(&p->contrib, (size_t)p->M * p->cs, "phased residual"));
+  TRY(wrk(&p->contrib, (size_t)(p->M + 1) * p->cs, "phased residual"));
   TRY(upload(p->kb_idx, kb_idx));
   TRY(upload(p->kb_w, kb_w));
   TRY(upload(p->phase, phase));
@@ -394,9 +425,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(upload(p->blade_frame_d, p->blade_frame));
   TRY(upload(p->order, order));
   if (!sitems.empty()) TRY(upload(p->sitems, sitems));
-  TRY(upload(p->cell_ids, cell_ids));
-  TRY(upload(p->cell_off, cell_off));
-  TRY(upload(p->cell_ent, cell_ent));
+  TRY(upload(p->sblob, blob));
   if (!items.empty()) TRY(upload(p->items, items));
   {
     cudaError_t e = fft_configure(n);
@@ -410,6 +439,8 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(tab(&p->status_dev, 1, "status word"));
   {
     cudaError_t e = cudaMemset(p->status_dev, 0, sizeof(int));
+    // the zero row that padding entries of the spread lists point at
+    if (e == cudaSuccess) e = cudaMemset(p->contrib + (size_t)p->M * p->cs, 0, (size_t)p->cs * sizeof(float2));
     if (e != cudaSuccess) {
       plan_free(p);
       return cuda_fail(e, "status word");
@@ -475,8 +506,9 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
   const size_t spread_items = (M * W * W + kSpreadCellCost * ncell) / kSpreadItemCost + 1;
   size_t b = 0;
   b += 4 * M + M * (W / 2) * 16 + (size_t)d->readout * Nf * 8 + 4 * N + 8 * n + 4 * B + 4 * M;  // sample tables
-  b += 16 * interp_items + 8 * spread_items + 4 * ncell + 4 * (ncell + 1) + 8 * M * W * W + 4;  // lists
-  b += 8 * T * n * n * cs + 8 * T * N * n * cs + 8 * M * cs;                                        // workspace
+  b += 16 * interp_items + 16 * spread_items + 8 * (ncell + spread_items) +
+       8 * (M * W * W + (kSpreadListPad - 1) * std::min(ncell, M * W * W));                          // lists
+  b += 8 * T * n * n * cs + 8 * T * N * n * cs + 8 * (M + 1) * cs;                                  // workspace
   b += 8 * M + 4 * 8 * vol + 64 + 2 * 8 * std::max<size_t>(32768, interp_items) + 8 +
        8 * std::max<size_t>((size_t)std::max(iters, 1), 64);                                           // optimiser
   b += 32 * 512;  // allocation rounding

@@ -16,6 +16,8 @@ constexpr int kInterpItem = 128;   // most samples per interpolation work item
 constexpr int kSpreadPatch = 8;        // spread cells are visited in 8x8-cell patches
 constexpr int kSpreadCellCost = 4;     // work of writing one cell, in list entries
 constexpr int kSpreadItemCost = 2048;  // target work per spread item
+constexpr int kSpreadListPad = 4;      // spread lists hold a multiple of this many entries
+constexpr int kSpreadStageInt2 = 6144; // shared-memory stage of one spread item, in int2 (48 KB)
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
 
@@ -87,18 +89,19 @@ struct Plan {
   int n_items = 0;
   int interp_tile = 16;          // TI: interpolation tile edge, cells
   // Spread gather: cells in patch-major order (frame, 8x8-cell patch,
-  // row-major in the patch), lists stored in that order.
-  int2* sitems = nullptr;        // [n_sitems] work items: [begin, end) in patch-major cell order
-  int* cell_ids = nullptr;       // [T * n * n] patch-major position -> cell index
-  int* cell_off = nullptr;       // [T * n * n + 1] list offsets per patch-major position
-  int2* cell_ent = nullptr;      // [cell_entries] (phased-residual offset m * cs, weight bits), ascending m
+  // row-major in the patch), cut into items; each item is one blob of
+  // (cell, list end) pairs followed by its cells' (offset m * cs, weight
+  // bits) lists, every list padded to kSpreadListPad entries with (M * cs, 0).
+  int4* sitems = nullptr;        // [n_sitems] (blob offset in int2, cells, entries, larger-than-a-stage flag)
+  int2* sblob = nullptr;         // [spread_entries] item blobs
   int n_sitems = 0;
-  size_t cell_entries = 0;
+  size_t spread_entries = 0;
+  bool spread_staged = true;     // every item fits a shared-memory stage
 
   // grid workspace (one bin chunk)
   float2* grid = nullptr;        // [T][n][n][chunk]
   float2* rows = nullptr;        // [T][N][n][chunk] row-pass intermediate
-  float2* contrib = nullptr;     // [M][chunk] conj(P[j][f]) r_m, input of the spread
+  float2* contrib = nullptr;     // [M + 1][cs] conj(P[j][f]) r_m, input of the spread; row M stays zero
 
   // reconstruction state (allocated on first use)
   bool recon_ready = false;

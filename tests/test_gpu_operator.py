@@ -68,6 +68,26 @@ def test_chunked_grid_matches_unchunked():
     _check(c, bin_chunk=4)
 
 
+@pytest.mark.parametrize("shape,bin_chunk", [
+    ((32, 15, 5, 8, 32, 1), 0),    # bin stride 16, last lane's second bin dead
+    ((32, 31, 4, 6, 32, 2), 0),    # bin stride 32, odd bin count, two frames
+    ((32, 63, 4, 6, 32, 1), 64),   # bin stride 64 (8-cell interpolation tiles)
+    ((32, 40, 4, 6, 32, 1), 32),   # chunks of 32 + 8: two-bin-per-lane then one-bin-per-lane kernels
+    ((32, 20, 3, 5, 32, 1), 16),   # chunks of 16 + 4
+])
+def test_bin_strides_and_ragged_chunks(shape, bin_chunk):
+    N, Nf, B, L, R, T = shape
+    c = random_case(N, Nf, B, L, R, T, seed=Nf + 100)
+    _check(c, bin_chunk=bin_chunk)
+
+
+def test_dense_blade_overlap_uses_global_lists():
+    """1400 blades through the k-space centre: the centre cells' spread lists
+    outgrow a shared-memory stage, so the plan gathers from global memory."""
+    c = random_case(16, 2, 1400, 2, 16, 1, seed=9)
+    _check(c)
+
+
 def test_tiny_workload_both_operators():
     w, p = workload_case("tiny")
     p["V"] = np.random.default_rng(11).standard_normal((1, 32, 32, 8)).astype(np.complex64)

@@ -255,9 +255,11 @@ PROP_API prop_status prop_tv_grad_static(const void* V_dev, int nframes, int n, 
 
 /* Stage profiling.  Stages: 0 forward row FFT, 1 forward column FFT,
  * 2 interpolation, 3 spread, 4 adjoint column FFT, 5 adjoint row FFT,
- * 6 TV + Adam (or TV gradient), 7 other (render).  While enabled, every
- * kernel launch of the plan is bracketed by two CUDA events on its stream. */
-#define PROP_NUM_STAGES 8
+ * 6 TV + Adam (or TV gradient), 7 other (render), 8 the fused row kernel of
+ * prop_reconstruct (adjoint row FFT + TV + Adam + the next iteration's
+ * forward row FFT).  While enabled, every kernel launch of the plan is
+ * bracketed by two CUDA events on its stream. */
+#define PROP_NUM_STAGES 9
 PROP_API prop_status prop_profile_enable(prop_plan plan, int enable);
 /* Synchronises on the recorded events, writes per-stage total milliseconds
  * and launch counts (arrays of PROP_NUM_STAGES), and clears the record. */

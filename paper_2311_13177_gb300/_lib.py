@@ -15,9 +15,9 @@ c_int, c_float, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_float, ct
                                                 ctypes.c_void_p, ctypes.c_size_t)
 
 PROP_OK = 0
-PROP_NUM_STAGES = 8
+PROP_NUM_STAGES = 9
 STAGE_NAMES = ["fft_fwd_rows", "fft_fwd_cols", "interp", "spread", "fft_adj_cols", "fft_adj_rows",
-               "tv_adam", "other"]
+               "tv_adam", "other", "rows_update"]
 STATUS_NAMES = {0: "PROP_OK", 1: "PROP_ERR_INVALID_ARG", 2: "PROP_ERR_OOM", 3: "PROP_ERR_CUDA",
                 4: "PROP_ERR_TIMEOUT", 5: "PROP_ERR_BUSY", 6: "PROP_ERR_NOT_READY",
                 7: "PROP_ERR_CANCELLED", 8: "PROP_ERR_UNIMPLEMENTED"}

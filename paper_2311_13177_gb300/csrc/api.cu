@@ -75,14 +75,15 @@ prop_status check_device_status(Plan& p) {
   return PROP_OK;
 }
 
-// y = A V, or r = A V - y_meas with |r|^2 reduced into *sumsq.
+// y = A V, or r = A V - y_meas with |r|^2 reduced into *sumsq.  rows_ready:
+// p.rows already holds the forward row transform of V (single chunk only).
 prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_meas, const Reducer* red,
-                         double* sumsq, cudaStream_t s) {
+                         double* sumsq, cudaStream_t s, bool rows_ready = false) {
   for (int c = 0; c < p.nchunks; ++c) {
     const int f0 = c * p.chunk;
     const int nb = std::min(p.chunk, p.Nf - f0);
     const bool last = c == p.nchunks - 1;
-    {
+    if (!(rows_ready && p.nchunks == 1)) {
       StageScope sc(p, kStFwdRows, s);
       PROP_LAUNCH(fft_forward_rows(p, V, f0, s));
     }
@@ -151,15 +152,36 @@ AdamArgs adam_args(const prop_recon_params* q, int k) {
   return a;
 }
 
+// One Adam iteration k from Vin into Vout.  With a single bin chunk the
+// last adjoint pass, the update and (next_rows) the next iteration's forward
+// row pass run as one fused kernel; rows_ready says that p.rows already holds
+// the forward row transform of Vin (left there by the previous iteration).
 prop_status step_impl(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin,
-                      float2* Vout, double* loss_dst, cudaStream_t s) {
+                      float2* Vout, double* loss_dst, cudaStream_t s, bool rows_ready = false,
+                      bool next_rows = false) {
   prop_status st;
   if (k == 1) {
     const size_t vbytes = p.vol_elems() * sizeof(float2);
     PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
     PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
   }
-  if ((st = forward_impl(p, Vin, p.resid, y, &p.red_interp, p.scalars, s)) != PROP_OK) return st;
+  const bool fused = p.nchunks == 1;
+  if ((st = forward_impl(p, Vin, p.resid, y, &p.red_interp, p.scalars, s, rows_ready && fused)) != PROP_OK)
+    return st;
+  if (fused) {
+    {
+      StageScope sc(p, kStSpread, s);
+      PROP_LAUNCH(spread(p, 0, p.Nf, p.resid, true, s));
+    }
+    {
+      StageScope sc(p, kStAdjCols, s);
+      PROP_LAUNCH(fft_adjoint_cols(p, s));
+    }
+    StageScope sc(p, kStFused, s);
+    PROP_LAUNCH(fused_rows_update(p, Vin, p.adam_m, p.adam_v, Vout, adam_args(q, k), &p.red_tv, p.scalars,
+                                  loss_dst, next_rows, s));
+    return PROP_OK;
+  }
   if ((st = adjoint_impl(p, p.resid, p.grad, true, s)) != PROP_OK) return st;
   StageScope sc(p, kStOpt, s);
   PROP_LAUNCH(tv_adam(p, Vin, p.grad, p.adam_m, p.adam_v, Vout, adam_args(q, k), &p.red_tv, p.scalars,
@@ -175,7 +197,7 @@ prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* 
   float2* cur = V;
   float2* nxt = p.vol2;
   for (int k = 1; k <= q->iters; ++k) {
-    if ((st = step_impl(p, y, q, k, cur, nxt, p.loss_dev + (k - 1), s)) != PROP_OK) return st;
+    if ((st = step_impl(p, y, q, k, cur, nxt, p.loss_dev + (k - 1), s, k > 1, k < q->iters)) != PROP_OK) return st;
     std::swap(cur, nxt);
   }
   if (cur != V) PROP_CUDA(cudaMemcpyAsync(V, cur, vbytes, cudaMemcpyDeviceToDevice, s));
@@ -190,8 +212,8 @@ prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* 
 }  // namespace
 
 prop_status plan_step(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin, float2* Vout,
-                      double* loss_dst, cudaStream_t s) {
-  return step_impl(p, y, q, k, Vin, Vout, loss_dst, s);
+                      double* loss_dst, cudaStream_t s, bool rows_ready, bool next_rows) {
+  return step_impl(p, y, q, k, Vin, Vout, loss_dst, s, rows_ready, next_rows);
 }
 
 }  // namespace prop

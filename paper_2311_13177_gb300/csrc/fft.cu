@@ -18,6 +18,7 @@
 // fly); intermediate passes exchange through shared memory in place.
 // Every thread holds E = 16 (n = 2^a) or 24 (n = 3 * 2^a) values per pass.
 #include "prop_internal.cuh"
+#include "tv_adam.cuh"
 
 namespace prop {
 namespace {
@@ -340,6 +341,129 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS) fft_kernel(FftArgs a) {
   }
 }
 
+// --- Fused row kernel: inverse row FFT -> TV + Adam -> next forward row FFT --
+//
+// With the whole bin range in one grid pass, the last adjoint pass (inverse
+// FFT along u1, crop, deapodise, scale), the optimiser update and the first
+// forward pass of the next iteration (deapodise, pad, FFT along x1) all work
+// on the same (t, i2) image row and 16 bins.  One CTA does the three in
+// turn: the gradient never goes to global memory, and the row workspace is
+// rewritten in place (each CTA reads its slice completely before writing it).
+// The arithmetic is that of the separate kernels, so the iterates are the
+// same bit for bit.
+struct FusedArgs {
+  float2* rows;        // [T][N][n][C] in: adjoint row intermediate, out: next forward row intermediate
+  const float* deapod;
+  const float2* twiddle;
+  const float2* Vin;
+  float2* Vout;
+  float2* m;
+  float2* v;
+  double* partials;
+  unsigned int* counter;
+  const double* data_loss;
+  double* loss_out;
+  int N, n, Nf, C, T;
+  float scale;         // adjoint scale (1/N)
+  AdamArgs ad;
+};
+
+// Adjoint output into the CTA's gradient buffer gb[i1][col].
+struct OutGrad {
+  float2* gb;
+  const float* dp;
+  int N, n;
+  float c2;
+  __device__ void operator()(int pos, int col, float2 val) const {
+    const int i1 = image_index(pos, N, n);
+    if (i1 >= 0) gb[i1 * kFftCols + col] = cscale(val, dp[i1] * c2);
+  }
+};
+// Forward input from the CTA's new-volume buffer vb[i1][col].
+struct InNewRow {
+  const float2* vb;
+  const float* dp;
+  int N, n;
+  float c2;
+  __device__ float2 operator()(int pos, int col) const {
+    const int i1 = image_index(pos, N, n);
+    if (i1 < 0) return make_float2(0.f, 0.f);
+    return cscale(vb[i1 * kFftCols + col], dp[i1] * c2);
+  }
+};
+
+// Register cap: 64 a thread for power-of-two lengths (two CTAs of 512
+// threads per SM), 128 for lengths with a factor 3 (24 values a thread).
+template <int NFFT>
+constexpr int fused_min_blocks() {
+  return 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
+}
+
+template <int NFFT, bool FWD_TAIL>
+__global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>())
+    fused_rows_kernel(FusedArgs a) {
+  extern __shared__ float2 smem[];
+  float2* X = smem;
+  float2* tw = smem + NFFT * kFftCols;
+  float2* gb = tw + NFFT;  // [N][kFftCols]
+  for (int i = threadIdx.x; i < NFFT; i += blockDim.x) tw[i] = a.twiddle[i];
+  __syncthreads();
+  const int col = threadIdx.x % kFftCols;
+  const int tl = threadIdx.x / kFftCols;
+  const size_t row = blockIdx.y;  // t*N + i2
+  const int i2 = (int)(row % a.N);
+  const int t = (int)(row / a.N);
+  const int fbase = blockIdx.x * kFftCols;
+  {
+    InAdjRows in{a.rows, a.n, a.C, a.Nf, fbase, row};
+    OutGrad out{gb, a.deapod, a.N, a.n, a.deapod[i2] * a.scale};
+    fft_pass<NFFT, +1, 0, 1>(X, tw, col, tl, in, out);
+  }
+  __syncthreads();
+  const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
+  float local = 0.f;
+  for (int e = threadIdx.x; e < a.N * kFftCols; e += blockDim.x) {
+    const int i1 = e / kFftCols;
+    const int f = fbase + (e % kFftCols);
+    float2 nx = make_float2(0.f, 0.f);
+    if (f < a.Nf) {
+      const size_t idx = (row * a.N + i1) * a.Nf + f;
+      const float2 x = a.Vin[idx];
+      float2 gxy, gt;
+      local += voxel_tv(a.Vin, idx, x, i1, i2, t, a.N, a.Nf, a.T, a.ad.tv_xy, a.ad.tv_t, eps2, &gxy, &gt);
+      const float2 g = total_grad(gb[e], gxy, gt, a.ad);
+      float2 mm = a.m[idx], vv = a.v[idx];
+      nx = adam_voxel(x, g, mm, vv, a.ad);
+      a.m[idx] = mm;
+      a.v[idx] = vv;
+      a.Vout[idx] = nx;
+    }
+    gb[e] = nx;
+  }
+  if constexpr (FWD_TAIL) {
+    __syncthreads();
+    InNewRow in{gb, a.deapod, a.N, a.n, a.deapod[i2]};
+    OutFwdRows out{a.rows, a.n, a.C, fbase, row};
+    fft_pass<NFFT, -1, 0, 1>(X, tw, col, tl, in, out);
+  }
+  finish_loss(local, a.partials, a.counter, a.data_loss, a.loss_out);
+}
+
+template <int NFFT>
+size_t fused_smem(int N) {
+  return Shape<NFFT>::SMEM + (size_t)N * kFftCols * sizeof(float2);
+}
+
+template <int NFFT>
+cudaError_t launch_fused(const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStream_t s) {
+  const size_t smem = fused_smem<NFFT>(a.N);
+  if (fwd_tail)
+    fused_rows_kernel<NFFT, true><<<grid, Shape<NFFT>::THREADS, smem, s>>>(a);
+  else
+    fused_rows_kernel<NFFT, false><<<grid, Shape<NFFT>::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int NFFT>
 cudaError_t launch(int kind, const FftArgs& a, dim3 grid, cudaStream_t s) {
   const size_t smem = Shape<NFFT>::SMEM;
@@ -360,7 +484,11 @@ cudaError_t configure_n() {
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kAdjCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-  return cudaFuncSetAttribute(fft_kernel<NFFT, kAdjRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kAdjRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  const int fsm = (int)fused_smem<NFFT>(NFFT / 2);
+  if ((e = cudaFuncSetAttribute(fused_rows_kernel<NFFT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
+    return e;
+  return cudaFuncSetAttribute(fused_rows_kernel<NFFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
 }
 
 #define PROP_FFT_SIZES(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
@@ -369,6 +497,16 @@ cudaError_t dispatch(int n, int kind, const FftArgs& a, dim3 grid, cudaStream_t 
   switch (n) {
 #define CASE(v) \
   case v: return launch<v>(kind, a, grid, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch_fused(int n, const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStream_t s) {
+  switch (n) {
+#define CASE(v) \
+  case v: return launch_fused<v>(a, fwd_tail, grid, s);
     PROP_FFT_SIZES(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -436,6 +574,34 @@ cudaError_t fft_adjoint_rows(const Plan& p, float2* out, int f0, float scale, cu
   a.Cv = std::min(p.chunk, p.Nf - f0);
   dim3 grid((a.Cv + kFftCols - 1) / kFftCols, p.T * p.N);
   return dispatch(p.n, kAdjRows, a, grid, s);
+}
+
+cudaError_t fused_rows_update(const Plan& p, const float2* Vin, float2* m, float2* v, float2* Vout,
+                              const AdamArgs& aa, const Reducer* red, const double* data_loss, double* loss_out,
+                              bool fwd_tail, cudaStream_t s) {
+  if (p.nchunks != 1 || !red) return cudaErrorInvalidValue;
+  FusedArgs a{};
+  a.rows = p.rows;
+  a.deapod = p.deapod;
+  a.twiddle = p.twiddle;
+  a.Vin = Vin;
+  a.Vout = Vout;
+  a.m = m;
+  a.v = v;
+  a.partials = red->partials;
+  a.counter = red->counter;
+  a.data_loss = data_loss;
+  a.loss_out = loss_out;
+  a.N = p.N;
+  a.n = p.n;
+  a.Nf = p.Nf;
+  a.C = p.cs;
+  a.T = p.T;
+  a.scale = 1.0f / (float)p.N;
+  a.ad = aa;
+  dim3 grid((p.Nf + kFftCols - 1) / kFftCols, p.T * p.N);
+  if ((long)grid.x * grid.y > red->capacity) return cudaErrorInvalidValue;
+  return dispatch_fused(p.n, a, fwd_tail, grid, s);
 }
 
 }  // namespace prop

@@ -13,6 +13,7 @@
 // voxel are read by other threads.  One thread per complex voxel, bins
 // fastest, so warps read and write contiguous runs.
 #include "prop_internal.cuh"
+#include "tv_adam.cuh"
 
 namespace prop {
 namespace {
@@ -52,24 +53,12 @@ struct OptArgs {
   AdamArgs p;
 };
 
-// d / sqrt(|d|^2 + eps^2) and sqrt(|d|^2 + eps^2)
-__device__ __forceinline__ float2 tv_term(float2 d, float eps2, float* mag) {
-  const float s = fmaf(d.x, d.x, fmaf(d.y, d.y, eps2));
-  const float inv = rsqrtf(s);
-  *mag = s * inv;
-  return make_float2(d.x * inv, d.y * inv);
-}
-
 template <bool ADAM>
 __global__ void __launch_bounds__(kOptThreads) opt_kernel(OptArgs a) {
   // Work unit: a segment of kSeg consecutive values of one image row (t, i2);
-  // a row holds N * Nf values (i1, f).  Boundary tests use offsets within the
-  // row, so no per-value division is needed.
+  // a row holds N * Nf values (i1, f).
   const float eps2 = a.p.tv_eps * a.p.tv_eps;
   const int rowlen = a.N * a.Nf;
-  const int sx = a.Nf;
-  const long sy = rowlen;
-  const long st = (long)a.N * rowlen;
   const int segs = (rowlen + kSeg - 1) / kSeg;
   const long nseg = (long)a.T * a.N * segs;
   float local = 0.f;
@@ -81,68 +70,14 @@ __global__ void __launch_bounds__(kOptThreads) opt_kernel(OptArgs a) {
     const long rbase = row * rowlen;
     for (int e = seg * kSeg + threadIdx.x; e < min(rowlen, (seg + 1) * kSeg); e += blockDim.x) {
       const long idx = rbase + e;
+      const int i1 = e / a.Nf;
       const float2 x = a.Vin[idx];
-      float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
-      float mag, sxy = 0.f, stt = 0.f;
-      if (a.p.tv_xy != 0.f) {
-        if (e + sx < rowlen) {
-          const float2 nb = a.Vin[idx + sx];
-          const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-          gxy.x -= q.x;
-          gxy.y -= q.y;
-          sxy += mag;
-        }
-        if (e >= sx) {
-          const float2 nb = a.Vin[idx - sx];
-          const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-          gxy.x += q.x;
-          gxy.y += q.y;
-        }
-        if (i2 + 1 < a.N) {
-          const float2 nb = a.Vin[idx + sy];
-          const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-          gxy.x -= q.x;
-          gxy.y -= q.y;
-          sxy += mag;
-        }
-        if (i2 > 0) {
-          const float2 nb = a.Vin[idx - sy];
-          const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-          gxy.x += q.x;
-          gxy.y += q.y;
-        }
-      }
-      if (a.p.tv_t != 0.f) {
-        if (t + 1 < a.T) {
-          const float2 nb = a.Vin[idx + st];
-          const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-          gt.x -= q.x;
-          gt.y -= q.y;
-          stt += mag;
-        }
-        if (t > 0) {
-          const float2 nb = a.Vin[idx - st];
-          const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-          gt.x += q.x;
-          gt.y += q.y;
-        }
-      }
-      local += a.p.tv_xy * sxy + a.p.tv_t * stt;
-      const float2 gd = a.g[idx];
-      float2 g;
-      g.x = fmaf(a.p.gscale, gd.x, fmaf(a.p.tv_xy, gxy.x, a.p.tv_t * gt.x));
-      g.y = fmaf(a.p.gscale, gd.y, fmaf(a.p.tv_xy, gxy.y, a.p.tv_t * gt.y));
+      float2 gxy, gt;
+      local += voxel_tv(a.Vin, (size_t)idx, x, i1, i2, t, a.N, a.Nf, a.T, a.p.tv_xy, a.p.tv_t, eps2, &gxy, &gt);
+      const float2 g = total_grad(a.g[idx], gxy, gt, a.p);
       if constexpr (ADAM) {
         float2 mm = a.m[idx], vv = a.v[idx];
-        mm.x = fmaf(a.p.beta1, mm.x, (1.f - a.p.beta1) * g.x);
-        mm.y = fmaf(a.p.beta1, mm.y, (1.f - a.p.beta1) * g.y);
-        vv.x = fmaf(a.p.beta2, vv.x, (1.f - a.p.beta2) * g.x * g.x);
-        vv.y = fmaf(a.p.beta2, vv.y, (1.f - a.p.beta2) * g.y * g.y);
-        const float dx = sqrtf(vv.x) * a.p.inv_bc2_sqrt + a.p.eps;
-        const float dy = sqrtf(vv.y) * a.p.inv_bc2_sqrt + a.p.eps;
-        float2 nx;
-        nx.x = x.x - a.p.lr_t * (mm.x / dx);
-        nx.y = x.y - a.p.lr_t * (mm.y / dy);
+        const float2 nx = adam_voxel(x, g, mm, vv, a.p);
         a.m[idx] = mm;
         a.v[idx] = vv;
         a.out[idx] = nx;
@@ -151,28 +86,7 @@ __global__ void __launch_bounds__(kOptThreads) opt_kernel(OptArgs a) {
       }
     }
   }
-  if (a.partials) {
-    __shared__ double sh[32];
-    __shared__ bool last;
-    const double bs = block_sum_d((double)local, sh);
-    if (threadIdx.x == 0) {
-      a.partials[blockIdx.x] = bs;
-      __threadfence();
-      const unsigned prev = atomicAdd(a.counter, 1u);
-      last = prev == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      double s = 0.0;
-      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&a.partials[i]);
-      s = block_sum_d(s, sh);
-      if (threadIdx.x == 0) {
-        *a.loss_out = s + (a.data_loss ? __ldcg(a.data_loss) : 0.0);
-        *a.counter = 0u;
-      }
-    }
-  }
+  if (a.partials) finish_loss(local, a.partials, a.counter, a.data_loss, a.loss_out);
 }
 
 __global__ void render_kernel(const float2* V, float2* img, long npix, int Nf, int lo, int hi) {
@@ -271,59 +185,13 @@ tv_grad_rows_kernel(const float2* V, float2* grad, double* scratch, double* loss
   const int row = blockIdx.x;  // t * N + i2
   const int i2 = row % N;
   const int t = row / N;
-  const long sy = rowlen;
-  const long st = (long)N * rowlen;
   const long rbase = (long)row * rowlen;
   float local = 0.f;
   for (int e = threadIdx.x; e < rowlen; e += blockDim.x) {
     const long idx = rbase + e;
     const float2 x = V[idx];
-    float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
-    float mag, sxy = 0.f, stt = 0.f;
-    if (tv_xy != 0.f) {
-      if (e + Nf < rowlen) {
-        const float2 nb = V[idx + Nf];
-        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-        gxy.x -= q.x;
-        gxy.y -= q.y;
-        sxy += mag;
-      }
-      if (e >= Nf) {
-        const float2 nb = V[idx - Nf];
-        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-        gxy.x += q.x;
-        gxy.y += q.y;
-      }
-      if (i2 + 1 < N) {
-        const float2 nb = V[idx + sy];
-        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-        gxy.x -= q.x;
-        gxy.y -= q.y;
-        sxy += mag;
-      }
-      if (i2 > 0) {
-        const float2 nb = V[idx - sy];
-        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-        gxy.x += q.x;
-        gxy.y += q.y;
-      }
-    }
-    if (tv_t != 0.f) {
-      if (t + 1 < T) {
-        const float2 nb = V[idx + st];
-        const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-        gt.x -= q.x;
-        gt.y -= q.y;
-        stt += mag;
-      }
-      if (t > 0) {
-        const float2 nb = V[idx - st];
-        const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-        gt.x += q.x;
-        gt.y += q.y;
-      }
-    }
-    local += tv_xy * sxy + tv_t * stt;
+    float2 gxy, gt;
+    local += voxel_tv(V, (size_t)idx, x, e / Nf, i2, t, N, Nf, T, tv_xy, tv_t, eps2, &gxy, &gt);
     grad[idx] = make_float2(fmaf(tv_xy, gxy.x, tv_t * gt.x), fmaf(tv_xy, gxy.y, tv_t * gt.y));
   }
   __shared__ double sh[32];

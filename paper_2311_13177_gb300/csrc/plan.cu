@@ -456,7 +456,8 @@ prop_status plan_ensure_recon(Plan* p, int iters) {
   prop_status st;
   if (!p->recon_ready) {
     const size_t nv = p->vol_elems();
-    const int red_cap = std::max(1 << 15, p->n_items);
+    const int fused_blocks = (p->Nf + kFftCols - 1) / kFftCols * p->T * p->N;  // fused row kernel's CTAs
+    const int red_cap = std::max(std::max(1 << 15, p->n_items), fused_blocks);
     if ((st = rec(&p->resid, (size_t)p->M, "residual")) != PROP_OK) return st;
     if ((st = rec(&p->grad, nv, "gradient")) != PROP_OK) return st;
     if ((st = rec(&p->vol2, nv, "volume buffer")) != PROP_OK) return st;
@@ -509,7 +510,7 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
   b += 16 * interp_items + 16 * spread_items + 8 * (ncell + spread_items) +
        8 * (M * W * W + (kSpreadListPad - 1) * std::min(ncell, M * W * W));                          // lists
   b += 8 * T * n * n * cs + 8 * T * N * n * cs + 8 * (M + 1) * cs;                                  // workspace
-  b += 8 * M + 4 * 8 * vol + 64 + 2 * 8 * std::max<size_t>(32768, interp_items) + 8 +
+  b += 8 * M + 4 * 8 * vol + 64 + 2 * 8 * std::max<size_t>(std::max<size_t>(32768, interp_items), (Nf + 15) / 16 * T * N) + 8 +
        8 * std::max<size_t>((size_t)std::max(iters, 1), 64);                                           // optimiser
   b += 32 * 512;  // allocation rounding
   return b;

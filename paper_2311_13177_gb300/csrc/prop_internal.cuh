@@ -131,7 +131,7 @@ struct Plan {
 };
 
 // Stage ids of prop_profile_read.
-enum Stage { kStFwdRows = 0, kStFwdCols, kStInterp, kStSpread, kStAdjCols, kStAdjRows, kStOpt, kStOther };
+enum Stage { kStFwdRows = 0, kStFwdCols, kStInterp, kStSpread, kStAdjCols, kStAdjRows, kStOpt, kStOther, kStFused };
 
 // Brackets one launch with profiling events when the plan profiles.
 struct StageScope {
@@ -153,8 +153,12 @@ prop_status plan_ensure_recon(Plan* p, int iters);
 // reconstructed (tables, workspace, optimiser state); 0 if `d` is invalid.
 size_t plan_estimate_bytes(const prop_plan_desc* d, int iters);
 // One Adam iteration k (1-based) from Vin into Vout; L(Vin) -> *loss_dst (device).
+// rows_ready: the plan's row workspace holds the forward row transform of Vin
+// (left by the previous step with next_rows); next_rows: leave the forward
+// row transform of Vout there.  Both only take effect with one bin chunk.
 prop_status plan_step(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin,
-                      float2* Vout, double* loss_dst, cudaStream_t s);
+                      float2* Vout, double* loss_dst, cudaStream_t s, bool rows_ready = false,
+                      bool next_rows = false);
 
 // fft.cu: the four line-FFT passes of the 2-D (i)FFT per bin chunk.
 // Forward: V chunk -> rows (deapodise, pad, FFT along x1) -> grid (pad, FFT along x2).
@@ -198,6 +202,14 @@ cudaError_t tv_grad(const Plan& p, const float2* V, const float2* g, float2* gra
                     const AdamArgs& a, const Reducer* red, const double* data_loss,
                     double* loss_out, cudaStream_t s);
 cudaError_t render(const Plan& p, const float2* V, int f_lo, int f_hi, float2* img, cudaStream_t s);
+
+// fft.cu, single bin chunk only: the inverse row FFT of p.rows (the last
+// adjoint pass) fused with TV + Adam (Vin -> Vout, moments m, v) and, with
+// fwd_tail, the forward row FFT of Vout into p.rows for the next iteration.
+// Loss as in tv_adam.
+cudaError_t fused_rows_update(const Plan& p, const float2* Vin, float2* m, float2* v, float2* Vout,
+                              const AdamArgs& aa, const Reducer* red, const double* data_loss, double* loss_out,
+                              bool fwd_tail, cudaStream_t s);
 
 }  // namespace prop
 

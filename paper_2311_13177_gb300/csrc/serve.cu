@@ -401,7 +401,10 @@ void scheduler(prop_server_s* s) {
       if (r->k < r->params.iters && r->inflight.size() < 2) {
         Plan& p = *r->plan;
         const int k = r->k + 1;
-        const prop_status st = plan_step(p, r->y_dev, &r->params, k, r->cur, r->nxt, p.loss_dev + (k - 1), r->stream);
+        // consecutive iterations of one request on its own plan: the fused
+        // row kernel hands the next forward row transform along
+        const prop_status st = plan_step(p, r->y_dev, &r->params, k, r->cur, r->nxt, p.loss_dev + (k - 1),
+                                         r->stream, k > 1, k < r->params.iters);
         if (st != PROP_OK) {
           const std::string msg = prop_last_error();
           cudaStreamSynchronize(r->stream);

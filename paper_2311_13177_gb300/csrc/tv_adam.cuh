@@ -1,0 +1,141 @@
+// Per-voxel smoothed-TV gradient and Adam update, shared by the optimiser
+// kernel and the fused inverse-FFT / update / forward-FFT row kernel so that
+// both paths run the same arithmetic (Sec. 4.3: Adam on the data term plus
+// total variation in space and, for dynamic series, time).
+#pragma once
+
+#include "prop_internal.cuh"
+
+namespace prop {
+
+// d / sqrt(|d|^2 + eps^2) and sqrt(|d|^2 + eps^2)
+__device__ __forceinline__ float2 tv_term(float2 d, float eps2, float* mag) {
+  const float s = fmaf(d.x, d.x, fmaf(d.y, d.y, eps2));
+  const float inv = rsqrtf(s);
+  *mag = s * inv;
+  return make_float2(d.x * inv, d.y * inv);
+}
+
+// TV gradients at voxel idx = ((t N + i2) N + i1) Nf + f of Vin (value x):
+// forward differences along x1, x2 and t, no wrap-around.  *gxy, *gt get the
+// gradients of TV_xy and TV_t; the return value is this voxel's own share of
+// the weighted TV value (the terms of the differences it is the lower end of).
+__device__ __forceinline__ float voxel_tv(const float2* __restrict__ Vin, size_t idx, float2 x, int i1, int i2,
+                                          int t, int N, int Nf, int T, float tv_xy, float tv_t, float eps2,
+                                          float2* gxy_out, float2* gt_out) {
+  const size_t sx = (size_t)Nf, sy = (size_t)N * Nf, st = (size_t)N * N * Nf;
+  float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
+  float mag, sxy = 0.f, stt = 0.f;
+  if (tv_xy != 0.f) {
+    if (i1 + 1 < N) {
+      const float2 nb = Vin[idx + sx];
+      const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+      gxy.x -= q.x;
+      gxy.y -= q.y;
+      sxy += mag;
+    }
+    if (i1 > 0) {
+      const float2 nb = Vin[idx - sx];
+      const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+      gxy.x += q.x;
+      gxy.y += q.y;
+    }
+    if (i2 + 1 < N) {
+      const float2 nb = Vin[idx + sy];
+      const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+      gxy.x -= q.x;
+      gxy.y -= q.y;
+      sxy += mag;
+    }
+    if (i2 > 0) {
+      const float2 nb = Vin[idx - sy];
+      const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+      gxy.x += q.x;
+      gxy.y += q.y;
+    }
+  }
+  if (tv_t != 0.f) {
+    if (t + 1 < T) {
+      const float2 nb = Vin[idx + st];
+      const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
+      gt.x -= q.x;
+      gt.y -= q.y;
+      stt += mag;
+    }
+    if (t > 0) {
+      const float2 nb = Vin[idx - st];
+      const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
+      gt.x += q.x;
+      gt.y += q.y;
+    }
+  }
+  *gxy_out = gxy;
+  *gt_out = gt;
+  return tv_xy * sxy + tv_t * stt;
+}
+
+// g = gscale * gd + tv_xy * gxy + tv_t * gt
+__device__ __forceinline__ float2 total_grad(float2 gd, float2 gxy, float2 gt, const AdamArgs& p) {
+  return make_float2(fmaf(p.gscale, gd.x, fmaf(p.tv_xy, gxy.x, p.tv_t * gt.x)),
+                     fmaf(p.gscale, gd.y, fmaf(p.tv_xy, gxy.y, p.tv_t * gt.y)));
+}
+
+// Bias-corrected Adam on the real and imaginary parts; updates mm, vv and
+// returns the new voxel value.
+__device__ __forceinline__ float2 adam_voxel(float2 x, float2 g, float2& mm, float2& vv, const AdamArgs& p) {
+  mm.x = fmaf(p.beta1, mm.x, (1.f - p.beta1) * g.x);
+  mm.y = fmaf(p.beta1, mm.y, (1.f - p.beta1) * g.y);
+  vv.x = fmaf(p.beta2, vv.x, (1.f - p.beta2) * g.x * g.x);
+  vv.y = fmaf(p.beta2, vv.y, (1.f - p.beta2) * g.y * g.y);
+  const float dx = sqrtf(vv.x) * p.inv_bc2_sqrt + p.eps;
+  const float dy = sqrtf(vv.y) * p.inv_bc2_sqrt + p.eps;
+  return make_float2(x.x - p.lr_t * (mm.x / dx), x.y - p.lr_t * (mm.y / dy));
+}
+
+// Block sum of one double per thread; valid in thread 0 (all threads call).
+__device__ __forceinline__ double block_sum_tv(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+// Deterministic loss: every block stores its partial TV sum, the last block
+// to arrive adds them in block order plus the data term and writes the loss.
+// Blocks are numbered linearly over a 2-D grid.
+__device__ __forceinline__ void finish_loss(float local, double* partials, unsigned int* counter,
+                                            const double* data_loss, double* loss_out) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const double bs = block_sum_tv((double)local, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = prev == nblk - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) s += __ldcg(&partials[i]);
+    s = block_sum_tv(s, sh);
+    if (threadIdx.x == 0) {
+      *loss_out = s + (data_loss ? __ldcg(data_loss) : 0.0);
+      *counter = 0u;
+    }
+  }
+}
+
+}  // namespace prop

@@ -51,20 +51,62 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
   return p;
 }
 
+// Twiddle tables, one per Stockham pass p >= 1 with stride NS and radix R:
+// entry [k][r] (k < NS, r < R) = exp(-2 pi i r k / (NS R)), so a butterfly
+// fetches its R factors with R/2 16-byte loads.  Offsets are even (every NS
+// and hence every table size is even), so the tables stay 16-byte aligned.
+template <int NFFT>
+__host__ __device__ constexpr int tw_offset(int pass) {
+  constexpr RadixPlan RP = radix_plan(NFFT);
+  int off = 0, ns = RP.r[0];
+  for (int q = 1; q < pass; ++q) {
+    off += ns * RP.r[q];
+    ns *= RP.r[q];
+  }
+  return off;
+}
+
 template <int NFFT>
 struct Shape {
   static constexpr int E = (NFFT % 3 == 0) ? 24 : 16;  // values per thread
   static constexpr int TPL = NFFT / E;                 // threads per line
   static constexpr int THREADS = TPL * kFftCols;
-  static constexpr size_t SMEM = (size_t)NFFT * kFftCols * sizeof(float2) + NFFT * sizeof(float2);
+  static constexpr int TW = tw_offset<NFFT>(radix_plan(NFFT).count);  // twiddle table entries
+  static constexpr size_t SMEM = (size_t)NFFT * kFftCols * sizeof(float2) + (size_t)TW * sizeof(float2);
 };
+
+// Fill the per-pass twiddle tables from the length-NFFT table exp(-2 pi i m / NFFT).
+template <int NFFT>
+__device__ void build_twiddles(float2* tws, const float2* __restrict__ base) {
+  constexpr RadixPlan RP = radix_plan(NFFT);
+  int ns = RP.r[0];
+  for (int p = 1; p < RP.count; ++p) {
+    const int R = RP.r[p];
+    const int off = tw_offset<NFFT>(p);
+    const int step = NFFT / (ns * R);
+    for (int idx = threadIdx.x; idx < ns * R; idx += blockDim.x) {
+      const int k = idx / R, r = idx - (idx / R) * R;
+      tws[off + idx] = base[r * k * step];
+    }
+    ns *= R;
+  }
+}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// Rounded product that is never contracted into a later add: the inputs of
+// the first butterfly round the same way in every kernel that builds them.
+__device__ __forceinline__ float2 cscale_rn(float2 a, float s) {
+  return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s));
+}
 // z * (SIGN i)
 template <int SIGN>
 __device__ __forceinline__ float2 mul_si(float2 z) {
@@ -138,8 +180,14 @@ struct Dft<3, SIGN> {
 };
 
 // One Stockham pass; recurses into the next pass at compile time.
-template <int NFFT, int SIGN, int PI, int NS, class In, class Out>
-__device__ __forceinline__ void fft_pass(float2* X, const float2* tw, int col, int tl, const In& in,
+// PIN: the input line is a zero-padded image line (image index i at
+// position i - N/2 mod n, N = n/2, zeros elsewhere); the first pass then
+// reads only the positions that hold image values, known at compile time
+// for radix 8 or 4 (r < R/4 or r >= 3R/4), and never touches the padding.
+// POUT likewise for a cropped output in the last pass: only the image
+// positions are formed and stored.
+template <int NFFT, int SIGN, int PI, int NS, bool PIN, bool POUT, class In, class Out>
+__device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, int tl, const In& in,
                                          const Out& out) {
   constexpr RadixPlan RP = radix_plan(NFFT);
   constexpr int R = RP.r[PI];
@@ -149,26 +197,49 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tw, int col, i
   constexpr int STRIDE = NFFT / R;
   constexpr bool FIRST = PI == 0;
   constexpr bool LAST = PI == RP.count - 1;
+  constexpr bool PRUNE_IN = FIRST && PIN && (R == 8 || R == 4);
+  constexpr bool PRUNE_OUT = LAST && POUT && (R == 8 || R == 4);
+  constexpr int Q = NFFT / 4;  // N / 2
   static_assert(E % R == 0, "radix must divide the per-thread count");
+  static_assert(!(FIRST && PIN) || PRUNE_IN, "padded input needs a first radix of 8 or 4");
   float2 v[E];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int j = tl + TPL * q;
     const int k = j % NS;
+    float2 w[R];
+    if constexpr (NS > 1) {
+      const float2* T = tws + tw_offset<NFFT>(PI) + k * R;
+      if constexpr (R % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h) {
+          const float4 t = reinterpret_cast<const float4*>(T)[h];
+          w[2 * h] = make_float2(t.x, t.y);
+          w[2 * h + 1] = make_float2(t.z, t.w);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[r] = T[r];
+      }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int pos = j + r * STRIDE;
       float2 x;
-      if constexpr (FIRST)
+      if constexpr (PRUNE_IN) {
+        if (r < R / 4)
+          x = in.at(pos + Q, col);
+        else if (r >= R - R / 4)
+          x = in.at(pos - 3 * Q, col);
+        else
+          x = make_float2(0.f, 0.f);
+      } else if constexpr (FIRST) {
         x = in(pos, col);
-      else
+      } else {
         x = X[pos * kFftCols + col];
+      }
       if constexpr (NS > 1) {
-        if (r > 0) {
-          float2 w = tw[r * k * (NFFT / (NS * R))];
-          if (SIGN > 0) w.y = -w.y;
-          x = cmul(x, w);
-        }
+        if (r > 0) x = SIGN < 0 ? cmul(x, w[r]) : cmulc(x, w[r]);
       }
       v[q * R + r] = x;
     }
@@ -184,14 +255,23 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tw, int col, i
       for (int r = 0; r < R; ++r) X[(d + r * NS) * kFftCols + col] = v[q * R + r];
     }
     __syncthreads();
-    fft_pass<NFFT, SIGN, PI + 1, NS * R>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, SIGN, PI + 1, NS * R, PIN, POUT>(X, tws, col, tl, in, out);
   } else {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int j = tl + TPL * q;
-      const int d = (j / NS) * NS * R + (j % NS);
+      const int d = (j / NS) * NS * R + (j % NS);  // = j: NS R = NFFT in the last pass
 #pragma unroll
-      for (int r = 0; r < R; ++r) out(d + r * NS, col, v[q * R + r]);
+      for (int r = 0; r < R; ++r) {
+        if constexpr (PRUNE_OUT) {
+          if (r < R / 4)
+            out.at(d + r * NS + Q, col, v[q * R + r]);
+          else if (r >= R - R / 4)
+            out.at(d + r * NS - 3 * Q, col, v[q * R + r]);
+        } else {
+          out(d + r * NS, col, v[q * R + r]);
+        }
+      }
     }
   }
 }
@@ -226,12 +306,10 @@ struct InFwdRows {
   int N, n, Nf, Cv, f0, fbase;
   size_t row;  // (t*N + i2)
   float c2;
-  __device__ float2 operator()(int pos, int col) const {
+  __device__ float2 at(int i1, int col) const {  // i1: image index
     const int f = fbase + col;
-    const int i1 = image_index(pos, N, n);
-    if (f >= Cv || i1 < 0) return make_float2(0.f, 0.f);
-    float2 x = __ldg(&V[(row * N + i1) * Nf + f0 + f]);
-    return cscale(x, dp[i1] * c2);
+    if (f >= Cv) return make_float2(0.f, 0.f);
+    return cscale_rn(__ldg(&V[(row * N + i1) * Nf + f0 + f]), dp[i1] * c2);
   }
 };
 struct OutFwdRows {
@@ -248,11 +326,7 @@ struct InFwdCols {
   const float2* rows;
   int N, n;
   size_t nq, q, t;
-  __device__ float2 operator()(int pos, int col) const {
-    const int i2 = image_index(pos, N, n);
-    if (i2 < 0) return make_float2(0.f, 0.f);
-    return __ldg(&rows[(t * N + i2) * nq + q + col]);
-  }
+  __device__ float2 at(int i2, int col) const { return __ldg(&rows[(t * N + i2) * nq + q + col]); }
 };
 struct OutFwdCols {
   float2* grid;
@@ -279,6 +353,7 @@ struct OutAdjCols {
     const int i2 = image_index(pos, N, n);
     if (i2 >= 0) rows[(t * N + i2) * nq + q + col] = val;
   }
+  __device__ void at(int i2, int col, float2 val) const { rows[(t * N + i2) * nq + q + col] = val; }
 };
 // Adjoint rows: rows[t][i2][u1][f] -> inverse FFT along u1, crop,
 // * scale c(i1) c(i2) -> out[t][i2][i1][f0 + f].
@@ -303,6 +378,10 @@ struct OutAdjRows {
     const int i1 = image_index(pos, N, n);
     if (f < Cv && i1 >= 0) out[(row * N + i1) * Nf + f0 + f] = cscale(val, dp[i1] * c2);
   }
+  __device__ void at(int i1, int col, float2 val) const {
+    const int f = fbase + col;
+    if (f < Cv) out[(row * N + i1) * Nf + f0 + f] = cscale(val, dp[i1] * c2);
+  }
 };
 
 template <int NFFT, int KIND>
@@ -310,7 +389,7 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS) fft_kernel(FftArgs a) {
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
-  for (int i = threadIdx.x; i < NFFT; i += blockDim.x) tw[i] = a.twiddle[i];
+  build_twiddles<NFFT>(tw, a.twiddle);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
@@ -320,24 +399,24 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS) fft_kernel(FftArgs a) {
     const int fbase = blockIdx.x * kFftCols;
     InFwdRows in{a.src, a.deapod, a.N, a.n, a.Nf, a.Cv, a.f0, fbase, row, a.deapod[i2]};
     OutFwdRows out{a.dst, a.n, a.C, fbase, row};
-    fft_pass<NFFT, -1, 0, 1>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   } else if constexpr (KIND == kFwdCols) {
     const size_t nq = (size_t)a.n * a.C;
     InFwdCols in{a.src, a.N, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
     OutFwdCols out{a.dst, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
-    fft_pass<NFFT, -1, 0, 1>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   } else if constexpr (KIND == kAdjCols) {
     const size_t nq = (size_t)a.n * a.C;
     InAdjCols in{a.src, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
     OutAdjCols out{a.dst, a.N, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
-    fft_pass<NFFT, +1, 0, 1>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   } else {
     const size_t row = blockIdx.y;
     const int i2 = (int)(row % a.N);
     const int fbase = blockIdx.x * kFftCols;
     InAdjRows in{a.src, a.n, a.C, a.Cv, fbase, row};
     OutAdjRows out{a.dst, a.deapod, a.N, a.n, a.Nf, a.Cv, a.f0, fbase, row, a.deapod[i2] * a.scale};
-    fft_pass<NFFT, +1, 0, 1>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   }
 }
 
@@ -378,6 +457,7 @@ struct OutGrad {
     const int i1 = image_index(pos, N, n);
     if (i1 >= 0) gb[i1 * kFftCols + col] = cscale(val, dp[i1] * c2);
   }
+  __device__ void at(int i1, int col, float2 val) const { gb[i1 * kFftCols + col] = cscale(val, dp[i1] * c2); }
 };
 // Forward input from the CTA's new-volume buffer vb[i1][col].
 struct InNewRow {
@@ -385,18 +465,16 @@ struct InNewRow {
   const float* dp;
   int N, n;
   float c2;
-  __device__ float2 operator()(int pos, int col) const {
-    const int i1 = image_index(pos, N, n);
-    if (i1 < 0) return make_float2(0.f, 0.f);
-    return cscale(vb[i1 * kFftCols + col], dp[i1] * c2);
-  }
+  __device__ float2 at(int i1, int col) const { return cscale_rn(vb[i1 * kFftCols + col], dp[i1] * c2); }
 };
 
 // Register cap: 64 a thread for power-of-two lengths (two CTAs of 512
 // threads per SM), 128 for lengths with a factor 3 (24 values a thread).
 template <int NFFT>
 constexpr int fused_min_blocks() {
-  return 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
+  return 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64)) > 16
+             ? 16
+             : 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
 }
 
 template <int NFFT, bool FWD_TAIL>
@@ -405,8 +483,8 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>()
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
-  float2* gb = tw + NFFT;  // [N][kFftCols]
-  for (int i = threadIdx.x; i < NFFT; i += blockDim.x) tw[i] = a.twiddle[i];
+  float2* gb = tw + Shape<NFFT>::TW;  // [N][kFftCols]
+  build_twiddles<NFFT>(tw, a.twiddle);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
@@ -417,26 +495,34 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>()
   {
     InAdjRows in{a.rows, a.n, a.C, a.Nf, fbase, row};
     OutGrad out{gb, a.deapod, a.N, a.n, a.deapod[i2] * a.scale};
-    fft_pass<NFFT, +1, 0, 1>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   }
   __syncthreads();
   const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
   float local = 0.f;
+  // The volumes and moments never alias: loads of later voxels may be issued
+  // ahead of the stores of earlier ones.
+  const float2* __restrict__ Vin = a.Vin;
+  float2* __restrict__ Vout = a.Vout;
+  float2* __restrict__ mom1 = a.m;
+  float2* __restrict__ mom2 = a.v;
+#pragma unroll 4
   for (int e = threadIdx.x; e < a.N * kFftCols; e += blockDim.x) {
     const int i1 = e / kFftCols;
     const int f = fbase + (e % kFftCols);
     float2 nx = make_float2(0.f, 0.f);
     if (f < a.Nf) {
       const size_t idx = (row * a.N + i1) * a.Nf + f;
-      const float2 x = a.Vin[idx];
+      const float2 x = Vin[idx];
       float2 gxy, gt;
-      local += voxel_tv(a.Vin, idx, x, i1, i2, t, a.N, a.Nf, a.T, a.ad.tv_xy, a.ad.tv_t, eps2, &gxy, &gt);
+      local = __fadd_rn(local, voxel_tv(Vin, idx, x, i1, i2, t, a.N, a.Nf, a.T, a.ad.tv_xy, a.ad.tv_t, eps2,
+                                        &gxy, &gt));
       const float2 g = total_grad(gb[e], gxy, gt, a.ad);
-      float2 mm = a.m[idx], vv = a.v[idx];
+      float2 mm = mom1[idx], vv = mom2[idx];
       nx = adam_voxel(x, g, mm, vv, a.ad);
-      a.m[idx] = mm;
-      a.v[idx] = vv;
-      a.Vout[idx] = nx;
+      mom1[idx] = mm;
+      mom2[idx] = vv;
+      Vout[idx] = nx;
     }
     gb[e] = nx;
   }
@@ -444,7 +530,7 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>()
     __syncthreads();
     InNewRow in{gb, a.deapod, a.N, a.n, a.deapod[i2]};
     OutFwdRows out{a.rows, a.n, a.C, fbase, row};
-    fft_pass<NFFT, -1, 0, 1>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   }
   finish_loss(local, a.partials, a.counter, a.data_loss, a.loss_out);
 }

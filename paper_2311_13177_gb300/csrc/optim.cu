@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kOptThreads) opt_kernel(OptArgs a) {
       const int i1 = e / a.Nf;
       const float2 x = a.Vin[idx];
       float2 gxy, gt;
-      local += voxel_tv(a.Vin, (size_t)idx, x, i1, i2, t, a.N, a.Nf, a.T, a.p.tv_xy, a.p.tv_t, eps2, &gxy, &gt);
+      local = __fadd_rn(local, voxel_tv(a.Vin, (size_t)idx, x, i1, i2, t, a.N, a.Nf, a.T, a.p.tv_xy, a.p.tv_t,
+                                        eps2, &gxy, &gt));
       const float2 g = total_grad(a.g[idx], gxy, gt, a.p);
       if constexpr (ADAM) {
         float2 mm = a.m[idx], vv = a.v[idx];

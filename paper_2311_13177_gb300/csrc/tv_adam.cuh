@@ -8,12 +8,22 @@
 
 namespace prop {
 
+// Every operation below is an explicitly rounded intrinsic or fmaf, so the
+// compiler has no contraction left to decide: the kernels that inline these
+// functions in different surroundings produce the same bits.
+
 // d / sqrt(|d|^2 + eps^2) and sqrt(|d|^2 + eps^2)
 __device__ __forceinline__ float2 tv_term(float2 d, float eps2, float* mag) {
   const float s = fmaf(d.x, d.x, fmaf(d.y, d.y, eps2));
   const float inv = rsqrtf(s);
-  *mag = s * inv;
-  return make_float2(d.x * inv, d.y * inv);
+  *mag = __fmul_rn(s, inv);
+  return make_float2(__fmul_rn(d.x, inv), __fmul_rn(d.y, inv));
+}
+__device__ __forceinline__ float2 csub_rn(float2 a, float2 b) {
+  return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 cadd_rn(float2 a, float2 b) {
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
 }
 
 // TV gradients at voxel idx = ((t N + i2) N + i1) Nf + f of Vin (value x):
@@ -28,68 +38,45 @@ __device__ __forceinline__ float voxel_tv(const float2* __restrict__ Vin, size_t
   float mag, sxy = 0.f, stt = 0.f;
   if (tv_xy != 0.f) {
     if (i1 + 1 < N) {
-      const float2 nb = Vin[idx + sx];
-      const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-      gxy.x -= q.x;
-      gxy.y -= q.y;
-      sxy += mag;
+      gxy = csub_rn(gxy, tv_term(csub_rn(Vin[idx + sx], x), eps2, &mag));
+      sxy = __fadd_rn(sxy, mag);
     }
-    if (i1 > 0) {
-      const float2 nb = Vin[idx - sx];
-      const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-      gxy.x += q.x;
-      gxy.y += q.y;
-    }
+    if (i1 > 0) gxy = cadd_rn(gxy, tv_term(csub_rn(x, Vin[idx - sx]), eps2, &mag));
     if (i2 + 1 < N) {
-      const float2 nb = Vin[idx + sy];
-      const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-      gxy.x -= q.x;
-      gxy.y -= q.y;
-      sxy += mag;
+      gxy = csub_rn(gxy, tv_term(csub_rn(Vin[idx + sy], x), eps2, &mag));
+      sxy = __fadd_rn(sxy, mag);
     }
-    if (i2 > 0) {
-      const float2 nb = Vin[idx - sy];
-      const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-      gxy.x += q.x;
-      gxy.y += q.y;
-    }
+    if (i2 > 0) gxy = cadd_rn(gxy, tv_term(csub_rn(x, Vin[idx - sy]), eps2, &mag));
   }
   if (tv_t != 0.f) {
     if (t + 1 < T) {
-      const float2 nb = Vin[idx + st];
-      const float2 q = tv_term(make_float2(nb.x - x.x, nb.y - x.y), eps2, &mag);
-      gt.x -= q.x;
-      gt.y -= q.y;
-      stt += mag;
+      gt = csub_rn(gt, tv_term(csub_rn(Vin[idx + st], x), eps2, &mag));
+      stt = __fadd_rn(stt, mag);
     }
-    if (t > 0) {
-      const float2 nb = Vin[idx - st];
-      const float2 q = tv_term(make_float2(x.x - nb.x, x.y - nb.y), eps2, &mag);
-      gt.x += q.x;
-      gt.y += q.y;
-    }
+    if (t > 0) gt = cadd_rn(gt, tv_term(csub_rn(x, Vin[idx - st]), eps2, &mag));
   }
   *gxy_out = gxy;
   *gt_out = gt;
-  return tv_xy * sxy + tv_t * stt;
+  return fmaf(tv_xy, sxy, __fmul_rn(tv_t, stt));
 }
 
 // g = gscale * gd + tv_xy * gxy + tv_t * gt
 __device__ __forceinline__ float2 total_grad(float2 gd, float2 gxy, float2 gt, const AdamArgs& p) {
-  return make_float2(fmaf(p.gscale, gd.x, fmaf(p.tv_xy, gxy.x, p.tv_t * gt.x)),
-                     fmaf(p.gscale, gd.y, fmaf(p.tv_xy, gxy.y, p.tv_t * gt.y)));
+  return make_float2(fmaf(p.gscale, gd.x, fmaf(p.tv_xy, gxy.x, __fmul_rn(p.tv_t, gt.x))),
+                     fmaf(p.gscale, gd.y, fmaf(p.tv_xy, gxy.y, __fmul_rn(p.tv_t, gt.y))));
 }
 
 // Bias-corrected Adam on the real and imaginary parts; updates mm, vv and
 // returns the new voxel value.
 __device__ __forceinline__ float2 adam_voxel(float2 x, float2 g, float2& mm, float2& vv, const AdamArgs& p) {
-  mm.x = fmaf(p.beta1, mm.x, (1.f - p.beta1) * g.x);
-  mm.y = fmaf(p.beta1, mm.y, (1.f - p.beta1) * g.y);
-  vv.x = fmaf(p.beta2, vv.x, (1.f - p.beta2) * g.x * g.x);
-  vv.y = fmaf(p.beta2, vv.y, (1.f - p.beta2) * g.y * g.y);
-  const float dx = sqrtf(vv.x) * p.inv_bc2_sqrt + p.eps;
-  const float dy = sqrtf(vv.y) * p.inv_bc2_sqrt + p.eps;
-  return make_float2(x.x - p.lr_t * (mm.x / dx), x.y - p.lr_t * (mm.y / dy));
+  const float c1 = __fsub_rn(1.f, p.beta1), c2 = __fsub_rn(1.f, p.beta2);
+  mm.x = fmaf(p.beta1, mm.x, __fmul_rn(c1, g.x));
+  mm.y = fmaf(p.beta1, mm.y, __fmul_rn(c1, g.y));
+  vv.x = fmaf(p.beta2, vv.x, __fmul_rn(__fmul_rn(c2, g.x), g.x));
+  vv.y = fmaf(p.beta2, vv.y, __fmul_rn(__fmul_rn(c2, g.y), g.y));
+  const float dx = fmaf(sqrtf(vv.x), p.inv_bc2_sqrt, p.eps);
+  const float dy = fmaf(sqrtf(vv.y), p.inv_bc2_sqrt, p.eps);
+  return make_float2(fmaf(-p.lr_t, __fdiv_rn(mm.x, dx), x.x), fmaf(-p.lr_t, __fdiv_rn(mm.y, dy), x.y));
 }
 
 // Block sum of one double per thread; valid in thread 0 (all threads call).

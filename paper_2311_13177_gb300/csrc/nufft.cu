@@ -86,6 +86,7 @@ struct InterpArgs {
   unsigned int* counter;
   double* sumsq_out;
   int* err;  // set to 1 when a bounded wait expires
+  const int* cta_off;  // CTA c takes items [cta_off[c], cta_off[c + 1]) (balanced at plan time)
   int n_items, R, n, C, Cv, f0, Nf;
   int TI, tps, nbuf;
   float scale;
@@ -346,7 +347,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kInterpConsumers = 16;                          // compute warps per CTA
+constexpr int kInterpConsumers = 24;                          // compute warps per CTA
 constexpr int kInterp2Threads = 32 * (kInterpConsumers + 1);  // plus one producer warp
 
 // Interpolation for the compile-time bin strides CS in {8, 16, 32, 64}.
@@ -392,7 +393,8 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
   if (warp == NCW) {
     if (lane == 0) {
       int k = 0;
-      for (int item = blockIdx.x; item < a.n_items; item += gridDim.x, ++k) {
+      const int it_end = a.cta_off[blockIdx.x + 1];
+      for (int item = a.cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
         const int b = k % a.nbuf;
         if (k >= a.nbuf && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / a.nbuf) - 1) & 1))) {
           s_abort = 1;
@@ -409,7 +411,8 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
     const int f_lo = 2 * sub;
     const bool b0 = f_lo < a.Cv, b1 = f_lo + 1 < a.Cv;
     int k = 0;
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x, ++k) {
+    const int it_end = a.cta_off[blockIdx.x + 1];
+    for (int item = a.cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
       const int b = k % a.nbuf;
       const ItemGeom g = item_geom(a, item);
       // lane L prefetches the warp's sample of round L / SPW, slot L % SPW
@@ -456,26 +459,23 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
           const int lc = (int)(packed & 0xffff) - g.c0;
           const int lr = (int)(packed >> 16) - g.r0;
           const float4* base = reinterpret_cast<const float4*>(tile + ((size_t)lr * HW + lc) * CS + f_lo);
-          float4 racc[W];
-#pragma unroll
-          for (int q = 0; q < W; ++q) {
-            racc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int c = 0; c < W; ++c) {
-              const float4 gv = base[(q * HW + c) * (CS / 2)];
-              racc[q].x = fmaf(w[c], gv.x, racc[q].x);
-              racc[q].y = fmaf(w[c], gv.y, racc[q].y);
-              racc[q].z = fmaf(w[c], gv.z, racc[q].z);
-              racc[q].w = fmaf(w[c], gv.w, racc[q].w);
-            }
-          }
+          // row sums over the x1 taps, folded into the x2 sum row by row
           float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
           for (int q = 0; q < W; ++q) {
-            acc.x = fmaf(w[W + q], racc[q].x, acc.x);
-            acc.y = fmaf(w[W + q], racc[q].y, acc.y);
-            acc.z = fmaf(w[W + q], racc[q].z, acc.z);
-            acc.w = fmaf(w[W + q], racc[q].w, acc.w);
+            float4 rs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+              const float4 gv = base[(q * HW + c) * (CS / 2)];
+              rs.x = fmaf(w[c], gv.x, rs.x);
+              rs.y = fmaf(w[c], gv.y, rs.y);
+              rs.z = fmaf(w[c], gv.z, rs.z);
+              rs.w = fmaf(w[c], gv.w, rs.w);
+            }
+            acc.x = fmaf(w[W + q], rs.x, acc.x);
+            acc.y = fmaf(w[W + q], rs.y, acc.y);
+            acc.z = fmaf(w[W + q], rs.z, acc.z);
+            acc.w = fmaf(w[W + q], rs.w, acc.w);
           }
           const float2 z0 = cmulf(P0, make_float2(acc.x, acc.y));
           const float2 z1 = cmulf(P1, make_float2(acc.z, acc.w));
@@ -837,7 +837,10 @@ cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_
   const int HW = p.interp_tile + p.W - 1;
   // tiles, then a full and an empty barrier per buffer
   const size_t smem = (size_t)a.nbuf * HW * HW * p.cs * sizeof(float2) + 2 * a.nbuf * sizeof(uint64_t);
-  const int blocks = std::min(p.n_items, p.num_sms);
+  a.cta_off = p.item_cta_off;
+  // the two-bin kernel runs exactly the plan's balanced CTAs; the
+  // one-bin kernel strides over the items
+  const int blocks = interp2_eligible(p.cs, nbins) ? p.interp_ctas : std::min(p.n_items, p.num_sms);
   if (red && red->capacity < blocks) return cudaErrorInvalidValue;
   const int lp = lanes_for(nbins);
   dim3 grid((unsigned)blocks);

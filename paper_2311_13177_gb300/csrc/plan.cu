@@ -90,7 +90,7 @@ void plan_dev_free(Plan* p, void* ptr) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->order, p->items, p->sitems, p->sblob, p->contrib, p->grid, p->rows,
+                  p->order, p->items, p->item_cta_off, p->sitems, p->sblob, p->contrib, p->grid, p->rows,
                   p->resid, p->grad, p->status_dev,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
@@ -279,12 +279,51 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
     std::vector<int> cnt(ntile + 1, 0);
     for (size_t m = 0; m < (size_t)p->M; ++m) cnt[tile_of(m) + 1]++;
     for (size_t t = 0; t < ntile; ++t) cnt[t + 1] += cnt[t];
-    for (size_t t = 0; t < ntile; ++t)
-      for (int s = cnt[t]; s < cnt[t + 1]; s += kInterpItem)
-        items.push_back(make_int4((int)t, s, std::min(kInterpItem, cnt[t + 1] - s), 0));
+    for (size_t t = 0; t < ntile; ++t) {
+      // a tile's run in ceil(c / kInterpItem) items of nearly equal size
+      const int c = cnt[t + 1] - cnt[t];
+      const int parts = (c + kInterpItem - 1) / kInterpItem;
+      for (int q = 0, s = cnt[t]; q < parts; ++q) {
+        const int sz = c / parts + (q < c % parts ? 1 : 0);
+        items.push_back(make_int4((int)t, s, sz, 0));
+        s += sz;
+      }
+    }
     for (size_t m = 0; m < (size_t)p->M; ++m) order[cnt[tile_of(m)]++] = (int)m;
   }
   p->n_items = (int)items.size();
+  // Static balance over the persistent CTAs (one per SM): longest item first
+  // to the least loaded CTA, with an item's cost its shared-memory traffic
+  // (W^2 taps of cs bins per sample plus the staged tile); each CTA's items
+  // are then stored contiguously, in tile order.
+  std::vector<int> cta_off;
+  {
+    const int P = std::max(1, std::min(p->num_sms, p->n_items));
+    const long tile_cost = (long)(TI + Wi - 1) * (TI + Wi - 1) * p->cs / 16;
+    auto cost = [&](const int4& it) { return (long)it.z * Wi * Wi * p->cs / 16 + tile_cost; };
+    std::vector<int> idx(items.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost(items[a]) > cost(items[b]); });
+    std::vector<long> load(P, 0);
+    std::vector<std::vector<int>> own(P);
+    for (int i : idx) {
+      int best = 0;
+      for (int c = 1; c < P; ++c)
+        if (load[c] < load[best]) best = c;
+      load[best] += cost(items[i]);
+      own[best].push_back(i);
+    }
+    std::vector<int4> sorted;
+    sorted.reserve(items.size());
+    cta_off.assign(P + 1, 0);
+    for (int c = 0; c < P; ++c) {
+      std::sort(own[c].begin(), own[c].end());
+      for (int i : own[c]) sorted.push_back(items[i]);
+      cta_off[c + 1] = (int)sorted.size();
+    }
+    items.swap(sorted);
+    p->interp_ctas = P;
+  }
   // The interpolation reads the per-sample tables in this sorted order, so that
   // an item's metadata is one contiguous run.
   {
@@ -412,6 +451,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(tab(&p->blade_frame_d, p->blade_frame.size(), "blade frames"));
   TRY(tab(&p->order, order.size(), "interpolation order"));
   TRY(tab(&p->items, std::max<size_t>(items.size(), 1), "interpolation items"));
+  TRY(tab(&p->item_cta_off, cta_off.size(), "interpolation item ranges"));
   TRY(tab(&p->sitems, std::max<size_t>(sitems.size(), 1), "spread items"));
   TRY(tab(&p->sblob, blob.size(), "spread lists"));
   TRY(wrk(&p->grid, (size_t)p->T * n * n * p->cs, "grid workspace"));
@@ -427,6 +467,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   if (!sitems.empty()) TRY(upload(p->sitems, sitems));
   TRY(upload(p->sblob, blob));
   if (!items.empty()) TRY(upload(p->items, items));
+  TRY(upload(p->item_cta_off, cta_off));
   {
     cudaError_t e = fft_configure(n);
     // The interpolation may use the device's whole opt-in shared memory.

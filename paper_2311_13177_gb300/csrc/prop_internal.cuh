@@ -85,8 +85,10 @@ struct Plan {
   float2* twiddle = nullptr;     // [n] exp(-2 pi i k / n)
   int* blade_frame_d = nullptr;  // [B]
   int* order = nullptr;          // [M] samples sorted by grid tile (interpolation order)
-  int4* items = nullptr;         // [n_items] (frame * tiles^2 + tile, first, count, 0)
+  int4* items = nullptr;         // [n_items] (frame * tiles^2 + tile, first, count, 0), grouped by CTA
+  int* item_cta_off = nullptr;   // [interp_ctas + 1] CTA c interpolates items [off[c], off[c + 1])
   int n_items = 0;
+  int interp_ctas = 1;           // persistent interpolation CTAs the items are balanced over
   int interp_tile = 16;          // TI: interpolation tile edge, cells
   // Spread gather: cells in patch-major order (frame, 8x8-cell patch,
   // row-major in the patch), cut into items; each item is one blob of

@@ -477,6 +477,12 @@ constexpr int fused_min_blocks() {
              : 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
 }
 
+// Asynchronous prefetch of a contiguous range into L2 (16-byte aligned
+// address, size a multiple of 16); no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int NFFT, bool FWD_TAIL>
 __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>())
     fused_rows_kernel(FusedArgs a) {
@@ -484,13 +490,30 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>()
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
   float2* gb = tw + Shape<NFFT>::TW;  // [N][kFftCols]
+  const size_t row = blockIdx.y;  // t*N + i2
+  const int i2 = (int)(row % a.N);
+  const int t = (int)(row / a.N);
+  if (threadIdx.x == 0) {
+    // the update's operands stream into L2 while the inverse FFT runs: this
+    // image row of V, m and v, and the neighbouring rows the TV terms read
+    const size_t rl = (size_t)a.N * a.Nf;
+    const uint32_t rb = (uint32_t)(rl * sizeof(float2));
+    prefetch_l2(a.Vin + row * rl, rb);
+    prefetch_l2(a.m + row * rl, rb);
+    prefetch_l2(a.v + row * rl, rb);
+    if (a.ad.tv_xy != 0.f) {
+      if (i2 + 1 < a.N) prefetch_l2(a.Vin + (row + 1) * rl, rb);
+      if (i2 > 0) prefetch_l2(a.Vin + (row - 1) * rl, rb);
+    }
+    if (a.ad.tv_t != 0.f) {
+      if (t + 1 < a.T) prefetch_l2(a.Vin + (row + a.N) * rl, rb);
+      if (t > 0) prefetch_l2(a.Vin + (row - a.N) * rl, rb);
+    }
+  }
   build_twiddles<NFFT>(tw, a.twiddle);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
-  const size_t row = blockIdx.y;  // t*N + i2
-  const int i2 = (int)(row % a.N);
-  const int t = (int)(row / a.N);
   const int fbase = blockIdx.x * kFftCols;
   {
     InAdjRows in{a.rows, a.n, a.C, a.Nf, fbase, row};

@@ -20,6 +20,7 @@
 // reproducible.
 #include "prop_internal.cuh"
 
+
 namespace prop {
 namespace {
 
@@ -606,6 +607,73 @@ __device__ __forceinline__ void gather_item2(const int2* cells, int ncells, int 
   }
 }
 
+// Grouped gather (plan lists built per 2 x 2-cell group): the CS / 2 lanes
+// of a group own two adjacent bins each and fetch every listed sample's
+// phased-residual row once (one 16-byte load a lane), adding it with the
+// entry's four weights to the four cells of the group held in registers.
+// A row is read once per group instead of once per covered cell, and each
+// cell still sums its own terms in ascending sample order (zero weights add
+// exact zeros), as a per-cell list would.  Entries come in batches of four
+// with the four row loads in flight together.  Warps claim groups from a
+// shared counter.  `base` points at the item's blob in shared memory.
+template <int CS>
+__device__ __forceinline__ void gather_groups(const int2* base, int ngroups, int nent, int lane, int* next,
+                                              float2* grid, const float2* contrib, int Cv, int n) {
+  constexpr int LPG = CS / 2;    // lanes per group
+  constexpr int GPW = 32 / LPG;  // groups per warp
+  const int sub = lane % LPG, slot = lane / LPG;
+  const int ngp = (ngroups + 1) & ~1;
+  const int* offs = reinterpret_cast<const int*>(base + ngp);
+  const float4* wts = reinterpret_cast<const float4*>(base + ngp + nent / 2);
+  const float2* cb = contrib + 2 * sub;
+  auto row = [&](int off) { return __ldg(reinterpret_cast<const float4*>(cb + off)); };
+  for (;;) {
+    int g0 = 0;
+    if (lane == 0) g0 = atomicAdd(next, GPW);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (g0 >= ngroups) break;
+    const int g = g0 + slot;
+    const bool ok = g < ngroups;
+    int cell0 = 0, beg = 0, end = 0;
+    if (ok) {
+      const int2 ge = base[g];
+      cell0 = ge.x;
+      end = ge.y;
+      beg = g > 0 ? base[g - 1].y : 0;
+    }
+    float4 acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int e = beg; e < end; e += 4) {
+      const int4 o = *reinterpret_cast<const int4*>(offs + e);
+      const float4 v[4] = {row(o.x), row(o.y), row(o.z), row(o.w)};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 w = wts[e + u];
+        const float wa[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[c].x = fmaf(wa[c], v[u].x, acc[c].x);
+          acc[c].y = fmaf(wa[c], v[u].y, acc[c].y);
+          acc[c].z = fmaf(wa[c], v[u].z, acc[c].z);
+          acc[c].w = fmaf(wa[c], v[u].w, acc[c].w);
+        }
+      }
+    }
+    if (ok) {
+      const bool l0 = 2 * sub < Cv, l1 = 2 * sub + 1 < Cv;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float4 o = acc[c];
+        if (!l0) o.x = o.y = 0.f;
+        if (!l1) o.z = o.w = 0.f;
+        reinterpret_cast<float4*>(grid + ((size_t)cell0 + (size_t)(c >> 1) * n + (c & 1)) * CS)[sub] = o;
+      }
+    }
+  }
+}
+
 constexpr int kSpreadConsumers = 16;                          // gather warps per CTA
 constexpr int kSpreadThreads = 32 * (kSpreadConsumers + 1);   // plus one producer warp
 
@@ -615,10 +683,10 @@ constexpr int kSpreadThreads = 32 * (kSpreadConsumers + 1);   // plus one produc
 // used it, so the lists come from shared memory and only the phased-residual
 // rows (mostly L1/L2 hits) are read from global memory.  Used when every
 // item fits a stage (the plan checks).
-template <int CS>
-__global__ void __launch_bounds__(kSpreadThreads, 2) spread_stage_kernel(float2* grid, const float2* contrib,
-                                                                        const int4* sitems, const int2* blob,
-                                                                        int n_items, int Cv, int* err) {
+template <int CS, bool GROUPED>
+__global__ void __launch_bounds__(kSpreadThreads, 2)
+    spread_stage_kernel(float2* grid, const float2* contrib, const int4* sitems, const int2* blob,
+                        const int* cta_off, int Cv, int n, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int NCW = kSpreadConsumers;
   constexpr int NBUF = 2;
@@ -626,6 +694,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) spread_stage_kernel(float2*
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)NBUF * kSpreadStageInt2 * sizeof(int2));
   uint64_t* empty = full + NBUF;
   __shared__ volatile int s_abort;
+  __shared__ int s_next[NBUF];  // grouped lists: next unclaimed group of the item in each stage
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int b = 0; b < NBUF; ++b) {
@@ -639,7 +708,8 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) spread_stage_kernel(float2*
   if (warp == NCW) {
     if (lane == 0) {
       int k = 0;
-      for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
+      const int it_end = cta_off[blockIdx.x + 1];
+      for (int item = cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
         const int b = k % NBUF;
         if (k >= NBUF && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / NBUF) - 1) & 1))) {
           s_abort = 1;
@@ -647,7 +717,8 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) spread_stage_kernel(float2*
         }
         if (s_abort) break;
         const int4 d = __ldg(&sitems[item]);
-        const uint32_t bytes = (uint32_t)((((d.y + 1) & ~1) + d.z) * sizeof(int2));
+        const uint32_t bytes = (uint32_t)d.w * (uint32_t)sizeof(int2);  // the item's blob, sized by the plan
+        s_next[b] = 0;  // published to the gather warps by the barrier phase
         mbar_expect_tx(&full[b], bytes);
         bulk_g2s(stage + (size_t)b * kSpreadStageInt2, blob + d.x, bytes, &full[b]);
       }
@@ -656,13 +727,17 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) spread_stage_kernel(float2*
     }
   } else {
     int k = 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
+    const int it_end = cta_off[blockIdx.x + 1];
+    for (int item = cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
       const int b = k % NBUF;
       const int4 d = __ldg(&sitems[item]);
       const int ncp = (d.y + 1) & ~1;
       if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NBUF) & 1))) s_abort = 1;
       if (s_abort) break;
-      gather_item2<CS>(stage + (size_t)b * kSpreadStageInt2, d.y, ncp, warp, NCW, lane, grid, contrib, Cv);
+      if constexpr (GROUPED)
+        gather_groups<CS>(stage + (size_t)b * kSpreadStageInt2, d.y, d.z, lane, &s_next[b], grid, contrib, Cv, n);
+      else
+        gather_item2<CS>(stage + (size_t)b * kSpreadStageInt2, d.y, ncp, warp, NCW, lane, grid, contrib, Cv);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
     }
@@ -792,10 +867,11 @@ cudaError_t nufft_configure(int smem_optin) {
   if (e != cudaSuccess) return e;
   if ((e = configure_interp<8>(smem_optin))) return e;
   const int st = (int)spread_stage_smem();
-  if ((e = cudaFuncSetAttribute(spread_stage_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
-  if ((e = cudaFuncSetAttribute(spread_stage_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
-  if ((e = cudaFuncSetAttribute(spread_stage_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
-  return cudaFuncSetAttribute(spread_stage_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
+#define SA(CSV, GR) \
+  if ((e = cudaFuncSetAttribute(spread_stage_kernel<CSV, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
+  SA(8, false) SA(16, false) SA(32, false) SA(64, false) SA(8, true) SA(16, true) SA(32, true) SA(64, true)
+#undef SA
+  return cudaSuccess;
 }
 
 int interp_buffers(const Plan& p) {
@@ -862,15 +938,23 @@ cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contr
     if (e != cudaSuccess) return e;
   }
   if (p.n_sitems == 0) return cudaSuccess;
-  if (p.spread_staged && (p.cs == 8 || p.cs == 16 || p.cs == 32 || p.cs == 64)) {
-    dim3 g((unsigned)std::max(1, std::min(p.n_sitems, 2 * p.num_sms)));
+  if (p.spread_grouped || (p.spread_staged && (p.cs == 8 || p.cs == 16 || p.cs == 32 || p.cs == 64))) {
+    dim3 g((unsigned)p.spread_ctas);  // the plan balanced the items over exactly these CTAs
     const size_t smem = spread_stage_smem();
-#define SS(CSV) \
-  spread_stage_kernel<CSV><<<g, kSpreadThreads, smem, s>>>(p.grid, p.contrib, p.sitems, p.sblob, p.n_sitems, nbins, p.status_dev)
-    if (p.cs == 32) SS(32);
-    else if (p.cs == 64) SS(64);
-    else if (p.cs == 16) SS(16);
-    else SS(8);
+#define SS(CSV, GR)                                                                                    \
+  spread_stage_kernel<CSV, GR><<<g, kSpreadThreads, smem, s>>>(p.grid, p.contrib, p.sitems, p.sblob, \
+                                                               p.sitem_cta_off, nbins, p.n, p.status_dev)
+    if (p.spread_grouped) {
+      if (p.cs == 32) SS(32, true);
+      else if (p.cs == 64) SS(64, true);
+      else if (p.cs == 16) SS(16, true);
+      else SS(8, true);
+    } else {
+      if (p.cs == 32) SS(32, false);
+      else if (p.cs == 64) SS(64, false);
+      else if (p.cs == 16) SS(16, false);
+      else SS(8, false);
+    }
 #undef SS
   } else {
     dim3 g((unsigned)std::max(1, std::min(p.n_sitems, 65535)));

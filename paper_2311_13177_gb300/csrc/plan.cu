@@ -48,6 +48,119 @@ bool fft_size_supported(int n) {
   return false;
 }
 
+// Grouped spread lists for the shared-memory staged spread kernel.  The
+// grid cells of every frame are cut into 2 x 2-cell groups; a group's list
+// holds every sample whose W x W footprint meets the group, in ascending m,
+// as (phased-residual offset m * cs, the sample's weight w2[a] w1[b] on each
+// of the group's four cells, row-major, zero where the footprint misses the
+// cell).  The weights are the FP64 products rounded once, as in the
+// interpolation's tables, so every cell accumulates the same terms in the
+// same order as a per-cell list would.  Every list is padded to a multiple
+// of four entries with (row M, zero weights), row M of the phased residual
+// being kept zero.  Groups are taken in frame, 4 x 4-group patch, row-major
+// order and cut into items of about equal work, each item one blob of int2
+// words staged by a single bulk copy:
+//   groups[ngp]      (first cell index, end of its list), ngp = ngroups rounded up to even
+//   offs[nent / 2]   nent int32 offsets (nent a multiple of 4)
+//   wts[2 nent]      nent float4 weights
+// Returns false when one group's list alone exceeds a stage.
+bool build_group_lists(const Plan& p, const std::vector<int>& first_tap, const std::vector<double>& wd,
+                       std::vector<int4>& sitems, std::vector<int2>& blob) {
+  const int n = p.n, W = p.W, G = kSpreadGroup, gps = n / G, PG = kSpreadGroupPatch;
+  static_assert(kSpreadGroup == 2, "four weights per entry");
+  const size_t LR = (size_t)p.L * p.R;
+  const size_t ngroup = (size_t)p.T * gps * gps;
+  auto axis_groups = [&](int first, int* out) {
+    int cnt = 0;
+    for (int a = 0; a < W; ++a) {
+      const int g = ((first + a) % n) / G;
+      bool seen = false;
+      for (int k = 0; k < cnt; ++k) seen = seen || out[k] == g;
+      if (!seen) out[cnt++] = g;
+    }
+    return cnt;
+  };
+  std::vector<int> gcnt(ngroup, 0);
+  for (size_t m = 0; m < (size_t)p.M; ++m) {
+    const size_t frame = (size_t)p.blade_frame[m / LR];
+    int gr[16], gc[16];
+    const int nr = axis_groups(first_tap[2 * m + 1], gr), nc = axis_groups(first_tap[2 * m], gc);
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < nc; ++b) gcnt[(frame * gps + gr[a]) * gps + gc[b]]++;
+  }
+  std::vector<int> glen(ngroup);
+  for (size_t g = 0; g < ngroup; ++g) glen[g] = (gcnt[g] + kSpreadListPad - 1) / kSpreadListPad * kSpreadListPad;
+  std::vector<int> gorder;
+  gorder.reserve(ngroup);
+  for (int t = 0; t < p.T; ++t)
+    for (int pr = 0; pr < gps / PG; ++pr)
+      for (int pc = 0; pc < gps / PG; ++pc)
+        for (int r = 0; r < PG; ++r)
+          for (int c = 0; c < PG; ++c) gorder.push_back((t * gps + pr * PG + r) * gps + pc * PG + c);
+  std::vector<int> item_of(ngroup), first(ngroup);
+  struct ItemSec { size_t offs, wts; };
+  std::vector<ItemSec> secs;
+  auto words = [](long ng, long ne) { return ((ng + 1) & ~1L) + ne / 2 + 2 * ne; };
+  size_t i = 0;
+  while (i < ngroup) {
+    size_t j = i;
+    long cost = 0, nent = 0;
+    while (j < ngroup) {
+      const int c = glen[gorder[j]];
+      if (words((long)(j + 1 - i), nent + c) > kSpreadStageInt2) {
+        if (j == i) return false;  // one group exceeds a stage
+        break;
+      }
+      nent += c;
+      cost += c + kSpreadGroupCost;
+      ++j;
+      if (cost >= kSpreadGroupItemCost) break;
+    }
+    const long ng = (long)(j - i), ngp = (ng + 1) & ~1L;
+    const size_t at = blob.size();
+    if (at + (size_t)words(ng, nent) > 0x7fffffffULL) return false;
+    sitems.push_back(make_int4((int)at, (int)ng, (int)nent, (int)words(ng, nent)));
+    secs.push_back({at + (size_t)ngp, at + (size_t)ngp + (size_t)nent / 2});
+    blob.resize(at + (size_t)words(ng, nent), make_int2(0, 0));
+    {
+      int* offs = reinterpret_cast<int*>(&blob[secs.back().offs]);
+      for (long q = 0; q < nent; ++q) offs[q] = (int)((size_t)p.M * p.cs);  // padding: the zero row
+    }
+    long e = 0;
+    for (size_t q = i; q < j; ++q) {
+      const int g = gorder[q];
+      item_of[g] = (int)sitems.size() - 1;
+      first[g] = (int)e;
+      e += glen[g];
+      const int t = g / (gps * gps), gr = (g / gps) % gps, gc = g % gps;
+      blob[at + (q - i)] = make_int2((int)(((size_t)t * n + (size_t)gr * G) * n + (size_t)gc * G), (int)e);
+    }
+    i = j;
+  }
+  std::vector<int> cursor(ngroup, 0);
+  for (size_t m = 0; m < (size_t)p.M; ++m) {
+    const size_t frame = (size_t)p.blade_frame[m / LR];
+    const int r0 = first_tap[2 * m + 1], c0 = first_tap[2 * m];
+    int gr[16], gc[16];
+    const int nr = axis_groups(r0, gr), nc = axis_groups(c0, gc);
+    for (int a = 0; a < nr; ++a)
+      for (int b = 0; b < nc; ++b) {
+        const int g = (int)((frame * gps + gr[a]) * gps + gc[b]);
+        const ItemSec& sec = secs[item_of[g]];
+        const size_t e = (size_t)first[g] + cursor[g]++;
+        float w[4];
+        for (int ii = 0; ii < G; ++ii)
+          for (int jj = 0; jj < G; ++jj) {
+            const int da = (gr[a] * G + ii - r0 + n) % n, db = (gc[b] * G + jj - c0 + n) % n;
+            w[ii * G + jj] = (da < W && db < W) ? (float)(wd[m * 2 * W + W + da] * wd[m * 2 * W + db]) : 0.f;
+          }
+        reinterpret_cast<int*>(&blob[sec.offs])[e] = (int)(m * (size_t)p.cs);
+        std::memcpy(&blob[sec.wts + 2 * e], w, sizeof(w));
+      }
+  }
+  return true;
+}
+
 struct DevAlloc {
   Plan* p;
   size_t* counter;
@@ -90,7 +203,7 @@ void plan_dev_free(Plan* p, void* ptr) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->order, p->items, p->item_cta_off, p->sitems, p->sblob, p->contrib, p->grid, p->rows,
+                  p->order, p->items, p->item_cta_off, p->sitems, p->sitem_cta_off, p->sblob, p->contrib, p->grid, p->rows,
                   p->resid, p->grad, p->status_dev,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
@@ -346,6 +459,14 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   // the patch) and cut into work items of about equal work (list entries plus
   // a fixed cost per written cell); patch order keeps the residual rows an
   // item reads within a small region of k-space.
+  std::vector<int4> sitems;
+  std::vector<int2> blob;
+  const int2 pad_entry = make_int2((int)((size_t)p->M * p->cs), 0);
+  p->spread_grouped = (p->cs == 8 || p->cs == 16 || p->cs == 32 || p->cs == 64) &&
+                      build_group_lists(*p, first_tap, wd, sitems, blob);
+  if (!p->spread_grouped) {
+  sitems.clear();
+  blob.clear();
   const size_t ncell = (size_t)p->T * n * n;
   std::vector<int> cell_cnt(ncell, 0);
   auto cell_of = [&](size_t m, int a, int b) {
@@ -378,11 +499,8 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   // (row M, weight 0): row M of the phased-residual buffer is kept zero, so
   // a padding entry adds an exact zero and the gather runs unpredicated.  A
   // cell whose list alone exceeds the staging capacity forms an item of its
-  // own (flag 1) and the plan then gathers from global memory.
+  // own and the plan then gathers from global memory.
   std::vector<int> cell_first(ncell + 1, 0);  // cell -> first entry in the item's entries
-  std::vector<int4> sitems;                   // (blob offset in int2, ncells, nent, big)
-  std::vector<int2> blob;
-  const int2 pad_entry = make_int2((int)((size_t)p->M * p->cs), 0);
   {
     auto padded = [](int c) { return (c + kSpreadListPad - 1) / kSpreadListPad * kSpreadListPad; };
     size_t i = 0;
@@ -400,13 +518,12 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
         if (cost >= kSpreadItemCost) break;
       }
       const size_t ncells = j - i, ncp = (ncells + 1) & ~(size_t)1;
-      const int big = (long)ncp + nent > kSpreadStageInt2 ? 1 : 0;
-      if (big) p->spread_staged = false;  // a list longer than a stage: gather from global memory
+      if ((long)ncp + nent > kSpreadStageInt2) p->spread_staged = false;  // longer than a stage: read from global
       if (blob.size() + ncp + nent > 0x7fffffffULL) {
         plan_free(p);
         return fail(PROP_ERR_INVALID_ARG, "plan_create: spread lists exceed 2^31 entries");
       }
-      sitems.push_back(make_int4((int)blob.size(), (int)ncells, (int)nent, big));
+      sitems.push_back(make_int4((int)blob.size(), (int)ncells, (int)nent, (int)(ncp + nent)));
       const size_t cells_at = blob.size(), ent_at = cells_at + ncp;
       blob.resize(ent_at + nent, pad_entry);
       long e = 0;
@@ -428,8 +545,50 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
         std::memcpy(&wbits, &w, sizeof(float));
         blob[cell_first[cell_of(m, a, b)]++] = make_int2((int)(m * (size_t)p->cs), wbits);
       }
+  }
+  // every item's blob (its word count is the staged copy's size) lies in the
+  // list array, and a staged item fits a stage
+  for (const int4& it : sitems) {
+    const bool staged = p->spread_grouped || p->spread_staged;
+    if (it.x < 0 || it.w < 0 || (size_t)it.x + (size_t)it.w > blob.size() || (staged && it.w > kSpreadStageInt2)) {
+      plan_free(p);
+      return fail(PROP_ERR_INVALID_ARG, "plan_create: inconsistent spread lists");
+    }
+  }
   p->n_sitems = (int)sitems.size();
   p->spread_entries = blob.size();
+  // Static balance of the spread items over the staged kernel's persistent
+  // CTAs (two per SM): longest first to the least loaded CTA; each CTA's
+  // items are stored contiguously, in k-space order.
+  std::vector<int> scta_off;
+  {
+    const int P = std::max(1, std::min(2 * p->num_sms, p->n_sitems));
+    auto cost = [&](const int4& it) {
+      return (long)it.z + (long)it.y * (p->spread_grouped ? kSpreadGroupCost : kSpreadCellCost);
+    };
+    std::vector<int> idx(sitems.size());
+    for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost(sitems[a]) > cost(sitems[b]); });
+    std::vector<long> load(P, 0);
+    std::vector<std::vector<int>> own(P);
+    for (int q : idx) {
+      int best = 0;
+      for (int c = 1; c < P; ++c)
+        if (load[c] < load[best]) best = c;
+      load[best] += cost(sitems[q]);
+      own[best].push_back(q);
+    }
+    std::vector<int4> sorted;
+    sorted.reserve(sitems.size());
+    scta_off.assign(P + 1, 0);
+    for (int c = 0; c < P; ++c) {
+      std::sort(own[c].begin(), own[c].end());  // k-space order within a CTA
+      for (int q : own[c]) sorted.push_back(sitems[q]);
+      scta_off[c + 1] = (int)sorted.size();
+    }
+    sitems.swap(sorted);
+    p->spread_ctas = P;
+  }
   if (blob.empty()) blob.push_back(pad_entry);
 
   DevAlloc tab{p, &p->table_bytes};
@@ -453,6 +612,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(tab(&p->items, std::max<size_t>(items.size(), 1), "interpolation items"));
   TRY(tab(&p->item_cta_off, cta_off.size(), "interpolation item ranges"));
   TRY(tab(&p->sitems, std::max<size_t>(sitems.size(), 1), "spread items"));
+  TRY(tab(&p->sitem_cta_off, scta_off.size(), "spread item ranges"));
   TRY(tab(&p->sblob, blob.size(), "spread lists"));
   TRY(wrk(&p->grid, (size_t)p->T * n * n * p->cs, "grid workspace"));
   TRY(wrk(&p->rows, (size_t)p->T * N * n * p->cs, "row workspace"));
@@ -465,6 +625,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(upload(p->blade_frame_d, p->blade_frame));
   TRY(upload(p->order, order));
   if (!sitems.empty()) TRY(upload(p->sitems, sitems));
+  TRY(upload(p->sitem_cta_off, scta_off));
   TRY(upload(p->sblob, blob));
   if (!items.empty()) TRY(upload(p->items, items));
   TRY(upload(p->item_cta_off, cta_off));
@@ -548,8 +709,9 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
   const size_t spread_items = (M * W * W + kSpreadCellCost * ncell) / kSpreadItemCost + 1;
   size_t b = 0;
   b += 4 * M + M * (W / 2) * 16 + (size_t)d->readout * Nf * 8 + 4 * N + 8 * n + 4 * B + 4 * M;  // sample tables
-  b += 16 * interp_items + 16 * spread_items + 8 * (ncell + spread_items) +
-       8 * (M * W * W + (kSpreadListPad - 1) * std::min(ncell, M * W * W));                          // lists
+  const size_t cell_lists = 8 * (ncell + spread_items) + 8 * (M * W * W + (kSpreadListPad - 1) * std::min(ncell, M * W * W));
+  const size_t group_lists = 8 * (ncell / 4) + 8 + (4 + 16) * 2 * 16 * M + 16 * (ncell / 4);  // items <= groups
+  b += 16 * interp_items + 16 * spread_items + std::max(cell_lists, group_lists) + 4 * 1024;  // lists
   b += 8 * T * n * n * cs + 8 * T * N * n * cs + 8 * (M + 1) * cs;                                  // workspace
   b += 8 * M + 4 * 8 * vol + 64 + 2 * 8 * std::max<size_t>(std::max<size_t>(32768, interp_items), (Nf + 15) / 16 * T * N) + 8 +
        8 * std::max<size_t>((size_t)std::max(iters, 1), 64);                                           // optimiser

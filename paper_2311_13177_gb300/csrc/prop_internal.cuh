@@ -18,6 +18,10 @@ constexpr int kSpreadCellCost = 4;     // work of writing one cell, in list entr
 constexpr int kSpreadItemCost = 2048;  // target work per spread item
 constexpr int kSpreadListPad = 4;      // spread lists hold a multiple of this many entries
 constexpr int kSpreadStageInt2 = 6144; // shared-memory stage of one spread item, in int2 (48 KB)
+constexpr int kSpreadGroup = 2;        // grouped spread: 2 x 2-cell groups
+constexpr int kSpreadGroupPatch = 4;   // groups are ordered in 4 x 4-group patches
+constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list entries
+constexpr int kSpreadGroupItemCost = 1024;  // target work per grouped spread item
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
 
@@ -94,11 +98,14 @@ struct Plan {
   // row-major in the patch), cut into items; each item is one blob of
   // (cell, list end) pairs followed by its cells' (offset m * cs, weight
   // bits) lists, every list padded to kSpreadListPad entries with (M * cs, 0).
-  int4* sitems = nullptr;        // [n_sitems] (blob offset in int2, cells, entries, larger-than-a-stage flag)
+  int4* sitems = nullptr;        // [n_sitems] (blob offset in int2, cells or groups, entries, blob words)
   int2* sblob = nullptr;         // [spread_entries] item blobs
+  int* sitem_cta_off = nullptr;  // [spread_ctas + 1] staged-spread CTA c takes items [off[c], off[c + 1])
   int n_sitems = 0;
+  int spread_ctas = 1;           // persistent staged-spread CTAs the items are balanced over
   size_t spread_entries = 0;
-  bool spread_staged = true;     // every item fits a shared-memory stage
+  bool spread_staged = true;     // cell lists: every item fits a shared-memory stage
+  bool spread_grouped = false;   // sblob/sitems hold grouped lists (2 x 2-cell groups), else cell lists
 
   // grid workspace (one bin chunk)
   float2* grid = nullptr;        // [T][n][n][chunk]

@@ -66,10 +66,18 @@ __host__ __device__ constexpr int tw_offset(int pass) {
   return off;
 }
 
+// Values per thread: 16 (two radix-8 butterflies a pass), 24 for lengths
+// with a factor 3.  (8 values a thread, twice the threads, measured slower
+// for the column passes at n = 512.)
 template <int NFFT>
+constexpr int kValsPlain = (NFFT % 3 == 0) ? 24 : 16;
+template <int NFFT>
+constexpr int kValsFused = (NFFT % 3 == 0) ? 24 : 16;
+
+template <int NFFT, int EV>
 struct Shape {
-  static constexpr int E = (NFFT % 3 == 0) ? 24 : 16;  // values per thread
-  static constexpr int TPL = NFFT / E;                 // threads per line
+  static constexpr int E = EV;                 // values per thread
+  static constexpr int TPL = NFFT / E;         // threads per line
   static constexpr int THREADS = TPL * kFftCols;
   static constexpr int TW = tw_offset<NFFT>(radix_plan(NFFT).count);  // twiddle table entries
   static constexpr size_t SMEM = (size_t)NFFT * kFftCols * sizeof(float2) + (size_t)TW * sizeof(float2);
@@ -186,13 +194,13 @@ struct Dft<3, SIGN> {
 // for radix 8 or 4 (r < R/4 or r >= 3R/4), and never touches the padding.
 // POUT likewise for a cropped output in the last pass: only the image
 // positions are formed and stored.
-template <int NFFT, int SIGN, int PI, int NS, bool PIN, bool POUT, class In, class Out>
+template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class In, class Out>
 __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, int tl, const In& in,
                                          const Out& out) {
   constexpr RadixPlan RP = radix_plan(NFFT);
   constexpr int R = RP.r[PI];
-  constexpr int E = Shape<NFFT>::E;
-  constexpr int TPL = Shape<NFFT>::TPL;
+  constexpr int E = EV;
+  constexpr int TPL = NFFT / EV;
   constexpr int NB = E / R;
   constexpr int STRIDE = NFFT / R;
   constexpr bool FIRST = PI == 0;
@@ -255,7 +263,7 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
       for (int r = 0; r < R; ++r) X[(d + r * NS) * kFftCols + col] = v[q * R + r];
     }
     __syncthreads();
-    fft_pass<NFFT, SIGN, PI + 1, NS * R, PIN, POUT>(X, tws, col, tl, in, out);
+    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT>(X, tws, col, tl, in, out);
   } else {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -385,7 +393,8 @@ struct OutAdjRows {
 };
 
 template <int NFFT, int KIND>
-__global__ void __launch_bounds__(Shape<NFFT>::THREADS) fft_kernel(FftArgs a) {
+__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS) fft_kernel(FftArgs a) {
+  constexpr int EV = kValsPlain<NFFT>;
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
@@ -399,24 +408,24 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS) fft_kernel(FftArgs a) {
     const int fbase = blockIdx.x * kFftCols;
     InFwdRows in{a.src, a.deapod, a.N, a.n, a.Nf, a.Cv, a.f0, fbase, row, a.deapod[i2]};
     OutFwdRows out{a.dst, a.n, a.C, fbase, row};
-    fft_pass<NFFT, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   } else if constexpr (KIND == kFwdCols) {
     const size_t nq = (size_t)a.n * a.C;
     InFwdCols in{a.src, a.N, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
     OutFwdCols out{a.dst, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
-    fft_pass<NFFT, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   } else if constexpr (KIND == kAdjCols) {
     const size_t nq = (size_t)a.n * a.C;
     InAdjCols in{a.src, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
     OutAdjCols out{a.dst, a.N, a.n, nq, (size_t)blockIdx.x * kFftCols, blockIdx.y};
-    fft_pass<NFFT, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   } else {
     const size_t row = blockIdx.y;
     const int i2 = (int)(row % a.N);
     const int fbase = blockIdx.x * kFftCols;
     InAdjRows in{a.src, a.n, a.C, a.Cv, fbase, row};
     OutAdjRows out{a.dst, a.deapod, a.N, a.n, a.Nf, a.Cv, a.f0, fbase, row, a.deapod[i2] * a.scale};
-    fft_pass<NFFT, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   }
 }
 
@@ -472,9 +481,9 @@ struct InNewRow {
 // threads per SM), 128 for lengths with a factor 3 (24 values a thread).
 template <int NFFT>
 constexpr int fused_min_blocks() {
-  return 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64)) > 16
+  return 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * (NFFT % 3 == 0 ? 128 : 64)) > 16
              ? 16
-             : 65536 / (Shape<NFFT>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
+             : 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
 }
 
 // Asynchronous prefetch of a contiguous range into L2 (16-byte aligned
@@ -484,12 +493,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 }
 
 template <int NFFT, bool FWD_TAIL>
-__global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>())
+__global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_min_blocks<NFFT>())
     fused_rows_kernel(FusedArgs a) {
+  constexpr int EV = kValsFused<NFFT>;
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
-  float2* gb = tw + Shape<NFFT>::TW;  // [N][kFftCols]
+  float2* gb = tw + Shape<NFFT, EV>::TW;  // [N][kFftCols]
   const size_t row = blockIdx.y;  // t*N + i2
   const int i2 = (int)(row % a.N);
   const int t = (int)(row / a.N);
@@ -518,7 +528,7 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>()
   {
     InAdjRows in{a.rows, a.n, a.C, a.Nf, fbase, row};
     OutGrad out{gb, a.deapod, a.N, a.n, a.deapod[i2] * a.scale};
-    fft_pass<NFFT, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   }
   __syncthreads();
   const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
@@ -553,30 +563,30 @@ __global__ void __launch_bounds__(Shape<NFFT>::THREADS, fused_min_blocks<NFFT>()
     __syncthreads();
     InNewRow in{gb, a.deapod, a.N, a.n, a.deapod[i2]};
     OutFwdRows out{a.rows, a.n, a.C, fbase, row};
-    fft_pass<NFFT, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   }
   finish_loss(local, a.partials, a.counter, a.data_loss, a.loss_out);
 }
 
 template <int NFFT>
 size_t fused_smem(int N) {
-  return Shape<NFFT>::SMEM + (size_t)N * kFftCols * sizeof(float2);
+  return Shape<NFFT, kValsFused<NFFT>>::SMEM + (size_t)N * kFftCols * sizeof(float2);
 }
 
 template <int NFFT>
 cudaError_t launch_fused(const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStream_t s) {
   const size_t smem = fused_smem<NFFT>(a.N);
   if (fwd_tail)
-    fused_rows_kernel<NFFT, true><<<grid, Shape<NFFT>::THREADS, smem, s>>>(a);
+    fused_rows_kernel<NFFT, true><<<grid, Shape<NFFT, kValsFused<NFFT>>::THREADS, smem, s>>>(a);
   else
-    fused_rows_kernel<NFFT, false><<<grid, Shape<NFFT>::THREADS, smem, s>>>(a);
+    fused_rows_kernel<NFFT, false><<<grid, Shape<NFFT, kValsFused<NFFT>>::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int NFFT>
 cudaError_t launch(int kind, const FftArgs& a, dim3 grid, cudaStream_t s) {
-  const size_t smem = Shape<NFFT>::SMEM;
-  const int threads = Shape<NFFT>::THREADS;
+  const size_t smem = Shape<NFFT, kValsPlain<NFFT>>::SMEM;
+  const int threads = Shape<NFFT, kValsPlain<NFFT>>::THREADS;
   switch (kind) {
     case kFwdRows: fft_kernel<NFFT, kFwdRows><<<grid, threads, smem, s>>>(a); break;
     case kFwdCols: fft_kernel<NFFT, kFwdCols><<<grid, threads, smem, s>>>(a); break;
@@ -588,7 +598,7 @@ cudaError_t launch(int kind, const FftArgs& a, dim3 grid, cudaStream_t s) {
 
 template <int NFFT>
 cudaError_t configure_n() {
-  const int smem = (int)Shape<NFFT>::SMEM;
+  const int smem = (int)Shape<NFFT, kValsPlain<NFFT>>::SMEM;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;

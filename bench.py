@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--bin-chunk", type=int, default=0, help="bins per grid pass (0: the plan's default)")
     ap.add_argument("--workload", choices=["static", "dynamic", "diff"], default=WORKLOAD,
                     help="the headline line is the static workload; the others are for comparison")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -345,7 +346,8 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     w_rank = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
     prob = synth.make_problem(w_rank)
-    plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=local)
+    plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=local,
+                bin_chunk=args.bin_chunk)
     params = ReconParams(iters=1, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
     y = torch.from_numpy(prob["y"]).to(dev)
     Va = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)

@@ -89,7 +89,7 @@ typedef struct prop_plan_desc {
   int nframes;            /* T >= 1 (1 = static) */
   const int* blade_frame; /* [nblades] frame t(b) in [0, T), or NULL = all frame 0 */
   int kb_width;           /* interpolation kernel width: 0 (default) or 6 */
-  int bin_chunk;          /* bins per oversampled-grid pass: 0 = auto (min(Nf, 32)), else 1..64.
+  int bin_chunk;          /* bins per oversampled-grid pass: 0 = auto (min(Nf, 64)), else 1..64.
                              Smaller chunks recompute the grid per chunk in less memory. */
   int device;             /* CUDA device ordinal */
 } prop_plan_desc;

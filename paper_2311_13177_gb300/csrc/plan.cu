@@ -265,7 +265,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   p->M = p->B * p->L * p->R;
   p->device = d->device;
   p->W = d->kb_width == 0 ? kKbWidthDefault : d->kb_width;
-  p->chunk = d->bin_chunk == 0 ? std::min(p->Nf, 32) : std::min(d->bin_chunk, p->Nf);
+  p->chunk = d->bin_chunk == 0 ? std::min(p->Nf, kMaxChunk) : std::min(d->bin_chunk, p->Nf);
   p->nchunks = (p->Nf + p->chunk - 1) / p->chunk;
   p->cs = p->chunk + (p->chunk & 1);  // even stride: staged grid rows are 16-byte runs
   p->theta.assign(d->theta, d->theta + p->B);
@@ -700,7 +700,7 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
   const size_t N = d->n, n = 2 * N, Nf = d->nf, B = d->nblades, T = d->nframes;
   const size_t M = B * (size_t)d->lines * d->readout;
   const size_t W = d->kb_width == 8 ? 8 : 6;
-  const size_t chunk = d->bin_chunk == 0 ? std::min<size_t>(Nf, 32) : std::min<size_t>(d->bin_chunk, Nf);
+  const size_t chunk = d->bin_chunk == 0 ? std::min<size_t>(Nf, kMaxChunk) : std::min<size_t>(d->bin_chunk, Nf);
   const size_t cs = chunk + (chunk & 1);
   const size_t TI = cs <= 32 ? 16 : 8;
   const size_t ncell = T * n * n;

@@ -16,7 +16,7 @@
 // directly (zero padding and deapodisation applied on the fly), the last
 // pass writes global memory directly (cropping and scaling applied on the
 // fly); intermediate passes exchange through shared memory in place.
-// Every thread holds E = 16 (n = 2^a) or 24 (n = 3 * 2^a) values per pass.
+// Every thread holds E = 16 (n = 2^a) or 12 (n = 3 * 2^a) values per pass.
 #include "prop_internal.cuh"
 #include "tv_adam.cuh"
 
@@ -28,6 +28,9 @@ struct RadixPlan {
   int r[8];
 };
 
+// Radices 8, 4, 2 then 3.  Lengths with a factor 3 use radix 4 instead of 8,
+// so that 12 values a thread (the least common multiple of the radices) hold
+// whole butterflies in every pass: half the registers of 24, twice the threads.
 __host__ __device__ constexpr RadixPlan radix_plan(int n) {
   RadixPlan p{0, {1, 1, 1, 1, 1, 1, 1, 1}};
   int m = n, threes = 0;
@@ -35,9 +38,13 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
     m /= 3;
     ++threes;
   }
-  while (m % 8 == 0) {
+  while (threes == 0 && m % 8 == 0) {
     p.r[p.count++] = 8;
     m /= 8;
+  }
+  while (threes > 0 && m % 4 == 0) {
+    p.r[p.count++] = 4;
+    m /= 4;
   }
   if (m % 4 == 0) {
     p.r[p.count++] = 4;
@@ -66,13 +73,13 @@ __host__ __device__ constexpr int tw_offset(int pass) {
   return off;
 }
 
-// Values per thread: 16 (two radix-8 butterflies a pass), 24 for lengths
-// with a factor 3.  (8 values a thread, twice the threads, measured slower
-// for the column passes at n = 512.)
+// Values per thread: 16 (two radix-8 butterflies a pass), 12 for lengths
+// with a factor 3 (radices 4, 2, 3).  (8 values a thread, twice the
+// threads, measured slower for the column passes at n = 512.)
 template <int NFFT>
-constexpr int kValsPlain = (NFFT % 3 == 0) ? 24 : 16;
+constexpr int kValsPlain = (NFFT % 3 == 0) ? 12 : 16;
 template <int NFFT>
-constexpr int kValsFused = (NFFT % 3 == 0) ? 24 : 16;
+constexpr int kValsFused = (NFFT % 3 == 0) ? 12 : 16;
 
 template <int NFFT, int EV>
 struct Shape {
@@ -477,13 +484,12 @@ struct InNewRow {
   __device__ float2 at(int i1, int col) const { return cscale_rn(vb[i1 * kFftCols + col], dp[i1] * c2); }
 };
 
-// Register cap: 64 a thread for power-of-two lengths (two CTAs of 512
-// threads per SM), 128 for lengths with a factor 3 (24 values a thread).
+// Register cap: 64 a thread (two CTAs of 512 threads per SM).
 template <int NFFT>
 constexpr int fused_min_blocks() {
-  return 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * (NFFT % 3 == 0 ? 128 : 64)) > 16
+  return 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * 64) > 16
              ? 16
-             : 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * (NFFT % 3 == 0 ? 128 : 64));
+             : 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * 64);
 }
 
 // Asynchronous prefetch of a contiguous range into L2 (16-byte aligned

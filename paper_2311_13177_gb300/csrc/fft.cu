@@ -19,6 +19,7 @@
 // Every thread holds E = 16 (n = 2^a) or 12 (n = 3 * 2^a) values per pass.
 #include "prop_internal.cuh"
 #include "tv_adam.cuh"
+#include "tma.cuh"
 
 namespace prop {
 namespace {
@@ -201,9 +202,16 @@ struct Dft<3, SIGN> {
 // for radix 8 or 4 (r < R/4 or r >= 3R/4), and never touches the padding.
 // POUT likewise for a cropped output in the last pass: only the image
 // positions are formed and stored.
-template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class In, class Out>
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// `hook` runs once, on every thread, right after the barrier that follows
+// the first pass (all reads of the first pass's input are then complete).
+template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class In, class Out,
+          class Hook = NoHook>
 __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, int tl, const In& in,
-                                         const Out& out) {
+                                         const Out& out, const Hook& hook = Hook()) {
   constexpr RadixPlan RP = radix_plan(NFFT);
   constexpr int R = RP.r[PI];
   constexpr int E = EV;
@@ -270,7 +278,8 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
       for (int r = 0; r < R; ++r) X[(d + r * NS) * kFftCols + col] = v[q * R + r];
     }
     __syncthreads();
-    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT>(X, tws, col, tl, in, out);
+    if constexpr (FIRST) hook();
+    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT>(X, tws, col, tl, in, out, hook);
   } else {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -492,12 +501,6 @@ constexpr int fused_min_blocks() {
              : 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * 64);
 }
 
-// Asynchronous prefetch of a contiguous range into L2 (16-byte aligned
-// address, size a multiple of 16); no completion to wait for.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 template <int NFFT, bool FWD_TAIL>
 __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_min_blocks<NFFT>())
     fused_rows_kernel(FusedArgs a) {
@@ -589,6 +592,113 @@ cudaError_t launch_fused(const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStrea
   return cudaGetLastError();
 }
 
+// --- Column passes staged by TMA ------------------------------------------
+//
+// Persistent CTAs walk the column tiles (16 adjacent (u1, bin) lines of one
+// frame); the next tile for a buffer is loaded by a tensor copy as soon as
+// the first pass of the tile in it has read it, so the input of the next
+// tiles streams in while this one is transformed.
+// Forward: the staged input is the N image rows of the row intermediate
+// (padding is never stored); adjoint: the 2N grid rows.
+struct InTile {
+  const float2* t;  // [rows][kFftCols]
+  __device__ float2 at(int i, int col) const { return t[i * kFftCols + col]; }
+  __device__ float2 operator()(int pos, int col) const { return t[pos * kFftCols + col]; }
+};
+
+struct ColArgs {
+  float2* dst;
+  const float2* twiddle;
+  int* err;
+  size_t nq;
+  int N, n, qtiles, ntiles, bh, nbox;
+};
+
+template <int NFFT, int KIND>
+constexpr int col_rows() {
+  return KIND == kFwdCols ? NFFT / 2 : NFFT;
+}
+// Tile buffers and CTAs per SM: the forward pass stages the N image rows in
+// one buffer (the next tile is requested once the first pass has read the
+// current one) with two CTAs per SM; the adjoint stages all 2N rows, double
+// buffered, with one CTA per SM.
+template <int KIND>
+constexpr int col_bufs() {
+  return KIND == kFwdCols ? 1 : 2;
+}
+template <int KIND>
+constexpr int col_ctas_per_sm() {
+  return KIND == kFwdCols ? 2 : 1;
+}
+template <int NFFT, int KIND>
+constexpr size_t col_smem() {
+  return (size_t)col_bufs<KIND>() * col_rows<NFFT, KIND>() * kFftCols * sizeof(float2) +
+         Shape<NFFT, kValsPlain<NFFT>>::SMEM + 2 * sizeof(uint64_t);
+}
+
+template <int NFFT, int KIND>
+__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ctas_per_sm<KIND>())
+    fft_cols_tma_kernel(const __grid_constant__ CUtensorMap tin, ColArgs a) {
+  constexpr int EV = kValsPlain<NFFT>;
+  constexpr int H = col_rows<NFFT, KIND>();
+  constexpr int NB = col_bufs<KIND>();
+  extern __shared__ __align__(128) float2 smem[];
+  float2* tiles = smem;                      // [NB][H][kFftCols]
+  float2* X = tiles + NB * H * kFftCols;     // [NFFT][kFftCols]
+  float2* tw = X + NFFT * kFftCols;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tw + Shape<NFFT, EV>::TW);
+  __shared__ volatile int s_abort;
+  const uint32_t tile_bytes = (uint32_t)(H * kFftCols * sizeof(float2));
+  auto issue = [&](int tile, int b) {
+    const int t = tile / a.qtiles, qt = tile - (tile / a.qtiles) * a.qtiles;
+    mbar_expect_tx(&full[b], tile_bytes);
+    for (int i = 0; i < a.nbox; ++i)
+      tma_load_3d(tiles + ((size_t)b * H + (size_t)i * a.bh) * kFftCols, &tin, qt * 2 * kFftCols, i * a.bh, t,
+                  &full[b]);
+  };
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NB; ++b) mbar_init(&full[b], 1);
+    fence_mbar_init();
+    s_abort = 0;
+    for (int b = 0; b < NB; ++b)
+      if ((int)(blockIdx.x + b * gridDim.x) < a.ntiles) issue(blockIdx.x + b * gridDim.x, b);
+  }
+  build_twiddles<NFFT>(tw, a.twiddle);
+  __syncthreads();
+  const int col = threadIdx.x % kFftCols;
+  const int tl = threadIdx.x / kFftCols;
+  int k = 0;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
+    const int b = k % NB;
+    if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NB) & 1))) s_abort = 1;
+    __syncthreads();  // the previous tile's last pass is done with X; all threads see s_abort
+    if (s_abort) break;
+    const size_t t = (size_t)(tile / a.qtiles);
+    const size_t q = (size_t)(tile - (tile / a.qtiles) * a.qtiles) * kFftCols;
+    const int next = tile + NB * (int)gridDim.x;
+    auto hook = [&]() {
+      if (threadIdx.x == 0 && next < a.ntiles) {
+        fence_proxy_async_smem();
+        issue(next, b);
+      }
+    };
+    InTile in{tiles + (size_t)b * H * kFftCols};
+    if constexpr (KIND == kFwdCols) {
+      OutFwdCols out{a.dst, a.n, a.nq, q, t};
+      fft_pass<NFFT, EV, -1, 0, 1, true, false>(X, tw, col, tl, in, out, hook);
+    } else {
+      OutAdjCols out{a.dst, a.N, a.n, a.nq, q, t};
+      fft_pass<NFFT, EV, +1, 0, 1, false, true>(X, tw, col, tl, in, out, hook);
+    }
+  }
+  if (s_abort && threadIdx.x == 0) {
+    atomicExch(a.err, 1);
+    // let copies this CTA issued and nobody consumed land (bounded)
+    for (int kk = k; kk < k + NB; ++kk)
+      if ((int)(blockIdx.x + kk * gridDim.x) < a.ntiles) mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
+  }
+}
+
 template <int NFFT>
 cudaError_t launch(int kind, const FftArgs& a, dim3 grid, cudaStream_t s) {
   const size_t smem = Shape<NFFT, kValsPlain<NFFT>>::SMEM;
@@ -610,6 +720,17 @@ cudaError_t configure_n() {
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kAdjCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
   if ((e = cudaFuncSetAttribute(fft_kernel<NFFT, kAdjRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  int optin = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev))) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+  if (col_smem<NFFT, kFwdCols>() <= (size_t)optin - 1024)
+    if ((e = cudaFuncSetAttribute(fft_cols_tma_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<NFFT, kFwdCols>())))
+      return e;
+  if (col_smem<NFFT, kAdjCols>() <= (size_t)optin - 1024)
+    if ((e = cudaFuncSetAttribute(fft_cols_tma_kernel<NFFT, kAdjCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<NFFT, kAdjCols>())))
+      return e;
   const int fsm = (int)fused_smem<NFFT>(NFFT / 2);
   if ((e = cudaFuncSetAttribute(fused_rows_kernel<NFFT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
     return e;
@@ -626,6 +747,61 @@ cudaError_t dispatch(int n, int kind, const FftArgs& a, dim3 grid, cudaStream_t 
 #undef CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int NFFT>
+cudaError_t launch_cols_tma(int kind, const CUtensorMap& tm, const ColArgs& a, int sms, cudaStream_t s) {
+  const int per_sm = kind == kFwdCols ? col_ctas_per_sm<kFwdCols>() : col_ctas_per_sm<kAdjCols>();
+  const dim3 grid((unsigned)std::max(1, std::min(a.ntiles, per_sm * sms)));
+  if (kind == kFwdCols)
+    fft_cols_tma_kernel<NFFT, kFwdCols><<<grid, Shape<NFFT, kValsPlain<NFFT>>::THREADS,
+                                          col_smem<NFFT, kFwdCols>(), s>>>(tm, a);
+  else
+    fft_cols_tma_kernel<NFFT, kAdjCols><<<grid, Shape<NFFT, kValsPlain<NFFT>>::THREADS,
+                                          col_smem<NFFT, kAdjCols>(), s>>>(tm, a);
+  return cudaGetLastError();
+}
+
+size_t cols_smem(int n, int kind) {
+  switch (n) {
+#define CASE(v) \
+  case v: return kind == kFwdCols ? col_smem<v, kFwdCols>() : col_smem<v, kAdjCols>();
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return (size_t)1 << 30;
+  }
+}
+
+cudaError_t dispatch_cols_tma(int n, int kind, const CUtensorMap& tm, const ColArgs& a, int sms, cudaStream_t s) {
+  switch (n) {
+#define CASE(v) \
+  case v: return launch_cols_tma<v>(kind, tm, a, sms, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Largest power of two <= 256 dividing h (the tensor copy's box height).
+int box_rows(int h) {
+  int b = 256;
+  while (b > 1 && h % b != 0) b >>= 1;
+  return b;
+}
+
+ColArgs col_args(const Plan& p, int kind) {
+  ColArgs a{};
+  a.dst = kind == kFwdCols ? p.grid : p.rows;
+  a.twiddle = p.twiddle;
+  a.err = p.status_dev;
+  a.nq = (size_t)p.n * p.cs;
+  a.N = p.N;
+  a.n = p.n;
+  a.qtiles = (int)(a.nq / kFftCols);
+  a.ntiles = a.qtiles * p.T;
+  a.bh = box_rows(kind == kFwdCols ? p.N : p.n);
+  a.nbox = (kind == kFwdCols ? p.N : p.n) / a.bh;
+  return a;
 }
 
 cudaError_t dispatch_fused(int n, const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStream_t s) {
@@ -674,7 +850,41 @@ cudaError_t fft_forward_rows(const Plan& p, const float2* V, int f0, cudaStream_
   return dispatch(p.n, kFwdRows, a, grid, s);
 }
 
+void fft_make_maps(Plan& p) {
+  p.cols_tma_fwd = p.cols_tma_adj = false;
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return;
+    }
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  if (p.cs % 2 != 0 || p.T > 65536) return;
+  const size_t nq = (size_t)p.n * p.cs;
+  auto make = [&](CUtensorMap* tm, float2* base, int h) {
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * nq), (cuuint64_t)h, (cuuint64_t)p.T};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * nq * sizeof(float)), (cuuint64_t)(2 * nq * h * sizeof(float))};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * kFftCols), (cuuint32_t)box_rows(h), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  const size_t room = (size_t)p.smem_optin - 1024;
+  p.cols_tma_fwd = cols_smem(p.n, kFwdCols) <= room && make(&p.tm_rows, p.rows, p.N);
+  p.cols_tma_adj = cols_smem(p.n, kAdjCols) <= room && make(&p.tm_grid, p.grid, p.n);
+}
+
 cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s) {
+  if (p.cols_tma_fwd) return dispatch_cols_tma(p.n, kFwdCols, p.tm_rows, col_args(p, kFwdCols), p.num_sms, s);
   FftArgs a = base_args(p);
   a.src = p.rows;
   a.dst = p.grid;
@@ -683,6 +893,7 @@ cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s) {
 }
 
 cudaError_t fft_adjoint_cols(const Plan& p, cudaStream_t s) {
+  if (p.cols_tma_adj) return dispatch_cols_tma(p.n, kAdjCols, p.tm_grid, col_args(p, kAdjCols), p.num_sms, s);
   FftArgs a = base_args(p);
   a.src = p.grid;
   a.dst = p.rows;

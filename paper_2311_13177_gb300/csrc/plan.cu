@@ -629,6 +629,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(upload(p->sblob, blob));
   if (!items.empty()) TRY(upload(p->items, items));
   TRY(upload(p->item_cta_off, cta_off));
+  fft_make_maps(*p);
   {
     cudaError_t e = fft_configure(n);
     // The interpolation may use the device's whole opt-in shared memory.

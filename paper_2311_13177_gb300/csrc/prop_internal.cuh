@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libprop.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -107,6 +108,12 @@ struct Plan {
   bool spread_staged = true;     // cell lists: every item fits a shared-memory stage
   bool spread_grouped = false;   // sblob/sitems hold grouped lists (2 x 2-cell groups), else cell lists
 
+  // TMA tensor maps of the column passes' inputs (row workspace, grid), and
+  // whether the staged column kernels run for this plan's size
+  CUtensorMap tm_rows;
+  CUtensorMap tm_grid;
+  bool cols_tma_fwd = false, cols_tma_adj = false;
+
   // grid workspace (one bin chunk)
   float2* grid = nullptr;        // [T][n][n][chunk]
   float2* rows = nullptr;        // [T][N][n][chunk] row-pass intermediate
@@ -177,6 +184,10 @@ cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s);
 cudaError_t fft_adjoint_cols(const Plan& p, cudaStream_t s);
 cudaError_t fft_adjoint_rows(const Plan& p, float2* out, int f0, float scale, cudaStream_t s);
 cudaError_t fft_configure(int n);
+// Builds the column passes' tensor maps (after the workspaces exist) and
+// decides whether the staged column kernels fit this plan; never fails the
+// plan (the unstaged kernels remain).
+void fft_make_maps(Plan& p);
 
 // nufft.cu
 // Interpolation of the grid chunk at every blade sample, times the

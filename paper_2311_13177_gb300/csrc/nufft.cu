@@ -639,7 +639,7 @@ constexpr int kSpreadThreads = 32 * (kSpreadConsumers + 1);   // plus one produc
 // rows (mostly L1/L2 hits) are read from global memory.  Used when every
 // item fits a stage (the plan checks).
 template <int CS, bool GROUPED>
-__global__ void __launch_bounds__(kSpreadThreads, 2)
+__global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
     spread_stage_kernel(float2* grid, const float2* contrib, const int4* sitems, const int2* blob,
                         const int* cta_off, int Cv, int n, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];

@@ -562,7 +562,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   // items are stored contiguously, in k-space order.
   std::vector<int> scta_off;
   {
-    const int P = std::max(1, std::min(2 * p->num_sms, p->n_sitems));
+    const int P = std::max(1, std::min(kSpreadCtasPerSm * p->num_sms, p->n_sitems));
     auto cost = [&](const int4& it) {
       return (long)it.z + (long)it.y * (p->spread_grouped ? kSpreadGroupCost : kSpreadCellCost);
     };

@@ -19,6 +19,7 @@ constexpr int kSpreadCellCost = 4;     // work of writing one cell, in list entr
 constexpr int kSpreadItemCost = 2048;  // target work per spread item
 constexpr int kSpreadListPad = 4;      // spread lists hold a multiple of this many entries
 constexpr int kSpreadStageInt2 = 6144; // shared-memory stage of one spread item, in int2 (48 KB)
+constexpr int kSpreadCtasPerSm = 2;    // persistent staged-spread CTAs per SM
 constexpr int kSpreadGroup = 2;        // grouped spread: 2 x 2-cell groups
 constexpr int kSpreadGroupPatch = 4;   // groups are ordered in 4 x 4-group patches
 constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list entries

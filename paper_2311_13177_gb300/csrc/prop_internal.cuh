@@ -13,7 +13,7 @@
 namespace prop {
 
 constexpr int kKbWidthDefault = 6; // taps per axis of the Kaiser-Bessel kernel (6 or 8)
-constexpr int kInterpItem = 128;   // most samples per interpolation work item
+constexpr int kInterpItem = 256;   // most samples per interpolation work item
 constexpr int kSpreadPatch = 8;        // spread cells are visited in 8x8-cell patches
 constexpr int kSpreadCellCost = 4;     // work of writing one cell, in list entries
 constexpr int kSpreadItemCost = 2048;  // target work per spread item

@@ -8,17 +8,20 @@ spectral bins over [-4, 4] px, 16 uniformly rotated blades x 24 lines x 256
 readout samples, complex64 data from a seeded 20-ellipse water/fat phantom.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --diff-study     (differentiation workload, grid store vs recompute)
 
 Prints one JSON line (rank 0).  Under torchrun every rank reconstructs its
 own independent problem (weak scaling, no data-path collective); the
 barrier and the max over ranks use torch.distributed.
 
-Timing: W untimed steps, then K steps each bracketed by CUDA events on the
-library's stream, with a 256 MiB write between steps to flush L2.  The
-library's own per-stage events give the dominant kernel's duration for the
-roofline object.  `e2e` times the host-buffer API (prop_reconstruct_host)
-with its copies.  The reference arm times the FP64 CPU oracle on a bounded
-sample of the same step (see `cpu_baseline.sample`).
+Timing: W untimed iterations, then one prop_reconstruct call of K iterations
+bracketed by CUDA events on the launching stream (each iteration streams a
+working set larger than the 129 MB L2).  A second, profiled call gives the
+per-stage times and the dominant kernel's duration for the roofline object;
+`l2_flushed_iters_per_s` repeats single steps with a 256 MiB write between
+them.  `e2e` times the host-buffer API (prop_reconstruct_host) with its
+copies.  The reference arm times the FP64 CPU oracle on a bounded sample of
+the same step (see `cpu_baseline.sample`).
 """
 from __future__ import annotations
 
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--bin-chunk", type=int, default=0, help="bins per grid pass (0: the plan's default)")
+    ap.add_argument("--diff-study", action="store_true",
+                    help="differentiation workload: grid store vs recompute (memory and time), one JSON line")
     ap.add_argument("--workload", choices=["static", "dynamic", "diff"], default=WORKLOAD,
                     help="the headline line is the static workload; the others are for comparison")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -501,9 +506,58 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_diff_study(args):
+    """Forward + backward through the autograd op at the differentiation
+    workload (384^2, 64 bins, 32 blades x 32 x 384) for several bin chunks.
+    Chunk 64 keeps the oversampled grid of every bin resident at once
+    ("store"); smaller chunks reuse one chunk-sized grid and recompute it per
+    chunk in both directions ("recompute").  Reports the plan's device bytes
+    and the time of one forward + backward (CUDA events, after warm-up)."""
+    import torch
+    import synth
+    from paper_2311_13177_gb300 import build as _b
+    _b.build()
+    from paper_2311_13177_gb300 import Plan, prop_apply
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS["diff"]
+    p = synth.make_problem(w)
+    dev = torch.device("cuda", 0)
+    y = torch.from_numpy(p["y"]).to(dev)
+    rows = []
+    for chunk in (8, 16, 32, 64):
+        plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T, bin_chunk=chunk)
+        V = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev, requires_grad=True)
+
+        def step():
+            r = prop_apply(V, plan) - y
+            loss = (r.real ** 2 + r.imag ** 2).sum()
+            loss.backward()
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        rows.append({"bin_chunk": chunk, "mode": "store" if chunk >= w.Nf else "recompute",
+                     "plan_device_bytes": plan.workspace_bytes(),
+                     "ms_forward_backward": e0.elapsed_time(e1) / reps})
+        plan.destroy()
+        del V
+    print(json.dumps({"study": "differentiation grid store vs recompute",
+                      "workload": "384x384, 64 bins, 32 blades x 32 lines x 384 readout, fp32",
+                      "note": "forward + backward of sum |A V - y|^2 through torch.autograd (prop_forward, prop_adjoint)",
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.diff_study:
+        run_diff_study(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

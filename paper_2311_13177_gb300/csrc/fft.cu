@@ -31,7 +31,8 @@ struct RadixPlan {
 
 // Radices 8, 4, 2 then 3.  Lengths with a factor 3 use radix 4 instead of 8,
 // so that 12 values a thread (the least common multiple of the radices) hold
-// whole butterflies in every pass: half the registers of 24, twice the threads.
+// whole butterflies in every pass: half the registers of 24, twice the threads;
+// a leftover factor 2 is merged with a 3 into one radix-6 pass.
 __host__ __device__ constexpr RadixPlan radix_plan(int n) {
   RadixPlan p{0, {1, 1, 1, 1, 1, 1, 1, 1}};
   int m = n, threes = 0;
@@ -50,6 +51,13 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
   if (m % 4 == 0) {
     p.r[p.count++] = 4;
     m /= 4;
+  }
+  if (m % 2 == 0 && threes > 0) {  // a leftover 2 and a 3 make one radix-6 pass
+    m /= 2;
+    --threes;
+    for (int i = 0; i < threes; ++i) p.r[p.count++] = 3;
+    p.r[p.count++] = 6;
+    return p;
   }
   if (m % 2 == 0) {
     p.r[p.count++] = 2;
@@ -192,6 +200,26 @@ struct Dft<3, SIGN> {
     v[0] = cadd(v[0], t);
     v[1] = cadd(m, d);
     v[2] = csub(m, d);
+  }
+};
+
+// 6 = 2 x 3: the three-point DFTs of the even and the odd inputs, then
+// X[k] = E[k] + w^k O[k] and X[k + 3] = E[k] - w^k O[k], w = exp(SIGN 2 pi i / 6).
+template <int SIGN>
+struct Dft<6, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    constexpr float s3 = 0.86602540378443865f;  // sqrt(3)/2
+    float2 a[3] = {v[0], v[2], v[4]}, b[3] = {v[1], v[3], v[5]};
+    Dft<3, SIGN>::run(a);
+    Dft<3, SIGN>::run(b);
+    const float2 t1 = make_float2(0.5f * b[1].x - SIGN * s3 * b[1].y, 0.5f * b[1].y + SIGN * s3 * b[1].x);
+    const float2 t2 = make_float2(-0.5f * b[2].x - SIGN * s3 * b[2].y, -0.5f * b[2].y + SIGN * s3 * b[2].x);
+    v[0] = cadd(a[0], b[0]);
+    v[3] = csub(a[0], b[0]);
+    v[1] = cadd(a[1], t1);
+    v[4] = csub(a[1], t1);
+    v[2] = cadd(a[2], t2);
+    v[5] = csub(a[2], t2);
   }
 };
 

@@ -23,7 +23,7 @@ constexpr int kSpreadCtasPerSm = 2;    // persistent staged-spread CTAs per SM
 constexpr int kSpreadGroup = 2;        // grouped spread: 2 x 2-cell groups
 constexpr int kSpreadGroupPatch = 4;   // groups are ordered in 4 x 4-group patches
 constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list entries
-constexpr int kSpreadGroupItemCost = 1024;  // target work per grouped spread item
+constexpr int kSpreadGroupItemCost = 2048;  // target work per grouped spread item
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
 

@@ -15,9 +15,11 @@
 // Adjoint: G'_{t,f}[cell] = sum_m w(m, cell) conj(P[j_m][f]) r_m.  The
 // phased residual contrib[m][f] = conj(P[j_m][f]) r_m is formed once per
 // sample (fused into the interpolation when the grid holds every bin), then
-// every grid cell gathers its plan-time list of (sample, weight) pairs in a
-// fixed order: no atomics, every cell written exactly once, bitwise
-// reproducible.
+// the grid is gathered from plan-time lists in a fixed order: every 2 x 2
+// group of cells reads each covering sample's phased residual once and adds
+// it with that sample's weight on each of its four cells (per-cell lists
+// where the stride or a list's length rules the groups out).  No atomics,
+// every cell written exactly once, bitwise reproducible.
 #include "prop_internal.cuh"
 #include "tma.cuh"
 

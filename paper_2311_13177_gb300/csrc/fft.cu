@@ -540,6 +540,9 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_
   const size_t row = blockIdx.y;  // t*N + i2
   const int i2 = (int)(row % a.N);
   const int t = (int)(row / a.N);
+  build_twiddles<NFFT>(tw, a.twiddle);
+  grid_dep_wait();
+  grid_dep_release();
   if (threadIdx.x == 0) {
     // the update's operands stream into L2 while the inverse FFT runs: this
     // image row of V, m and v, and the neighbouring rows the TV terms read
@@ -557,7 +560,6 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_
       if (t > 0) prefetch_l2(a.Vin + (row - a.N) * rl, rb);
     }
   }
-  build_twiddles<NFFT>(tw, a.twiddle);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
@@ -613,11 +615,9 @@ size_t fused_smem(int N) {
 template <int NFFT>
 cudaError_t launch_fused(const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStream_t s) {
   const size_t smem = fused_smem<NFFT>(a.N);
-  if (fwd_tail)
-    fused_rows_kernel<NFFT, true><<<grid, Shape<NFFT, kValsFused<NFFT>>::THREADS, smem, s>>>(a);
-  else
-    fused_rows_kernel<NFFT, false><<<grid, Shape<NFFT, kValsFused<NFFT>>::THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  const dim3 block(Shape<NFFT, kValsFused<NFFT>>::THREADS);
+  if (fwd_tail) return launch_dep(fused_rows_kernel<NFFT, true>, grid, block, smem, s, a);
+  return launch_dep(fused_rows_kernel<NFFT, false>, grid, block, smem, s, a);
 }
 
 // --- Column passes staged by TMA ------------------------------------------
@@ -688,10 +688,13 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ct
     for (int b = 0; b < NB; ++b) mbar_init(&full[b], 1);
     fence_mbar_init();
     s_abort = 0;
-    for (int b = 0; b < NB; ++b)
-      if ((int)(blockIdx.x + b * gridDim.x) < a.ntiles) issue(blockIdx.x + b * gridDim.x, b);
   }
   build_twiddles<NFFT>(tw, a.twiddle);
+  grid_dep_wait();
+  grid_dep_release();
+  if (threadIdx.x == 0)
+    for (int b = 0; b < NB; ++b)
+      if ((int)(blockIdx.x + b * gridDim.x) < a.ntiles) issue(blockIdx.x + b * gridDim.x, b);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
@@ -781,13 +784,10 @@ template <int NFFT>
 cudaError_t launch_cols_tma(int kind, const CUtensorMap& tm, const ColArgs& a, int sms, cudaStream_t s) {
   const int per_sm = kind == kFwdCols ? col_ctas_per_sm<kFwdCols>() : col_ctas_per_sm<kAdjCols>();
   const dim3 grid((unsigned)std::max(1, std::min(a.ntiles, per_sm * sms)));
+  const dim3 block(Shape<NFFT, kValsPlain<NFFT>>::THREADS);
   if (kind == kFwdCols)
-    fft_cols_tma_kernel<NFFT, kFwdCols><<<grid, Shape<NFFT, kValsPlain<NFFT>>::THREADS,
-                                          col_smem<NFFT, kFwdCols>(), s>>>(tm, a);
-  else
-    fft_cols_tma_kernel<NFFT, kAdjCols><<<grid, Shape<NFFT, kValsPlain<NFFT>>::THREADS,
-                                          col_smem<NFFT, kAdjCols>(), s>>>(tm, a);
-  return cudaGetLastError();
+    return launch_dep(fft_cols_tma_kernel<NFFT, kFwdCols>, grid, block, col_smem<NFFT, kFwdCols>(), s, tm, a);
+  return launch_dep(fft_cols_tma_kernel<NFFT, kAdjCols>, grid, block, col_smem<NFFT, kAdjCols>(), s, tm, a);
 }
 
 size_t cols_smem(int n, int kind) {

@@ -346,6 +346,8 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
     s_abort = 0;
   }
   __syncthreads();
+  grid_dep_wait();
+  grid_dep_release();
 
   float sumsq = 0.f;
   if (warp == NCW) {
@@ -662,7 +664,12 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
     s_abort = 0;
   }
   __syncthreads();
+  // The producer reads only plan tables and writes shared memory: its first
+  // copies go out before the predecessor kernel has finished.  The gather
+  // warps read the phased residual and overwrite the grid, both shared with
+  // earlier kernels, so they wait.
   if (warp == NCW) {
+    grid_dep_release();
     if (lane == 0) {
       int k = 0;
       const int it_end = cta_off[blockIdx.x + 1];
@@ -683,6 +690,8 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
         mbar_wait_bounded(&full[kk % NBUF], (uint32_t)((kk / NBUF) & 1));
     }
   } else {
+    grid_dep_wait();
+    grid_dep_release();
     int k = 0;
     const int it_end = cta_off[blockIdx.x + 1];
     for (int item = cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
@@ -777,10 +786,11 @@ cudaError_t launch_interp(int lp, int cs, const InterpArgs& a, dim3 grid, size_t
   // compile-time strides for the common chunk widths when more than half of
   // the bins are live (two bins per lane), runtime stride otherwise
   if (interp2_eligible(cs, a.Cv)) {
-    if (cs == 32) interp2_kernel<32, W><<<grid, kInterp2Threads, smem, s>>>(a);
-    else if (cs == 64) interp2_kernel<64, W><<<grid, kInterp2Threads, smem, s>>>(a);
-    else if (cs == 16) interp2_kernel<16, W><<<grid, kInterp2Threads, smem, s>>>(a);
-    else interp2_kernel<8, W><<<grid, kInterp2Threads, smem, s>>>(a);
+    const dim3 block(kInterp2Threads);
+    if (cs == 32) return launch_dep(interp2_kernel<32, W>, grid, block, smem, s, a);
+    if (cs == 64) return launch_dep(interp2_kernel<64, W>, grid, block, smem, s, a);
+    if (cs == 16) return launch_dep(interp2_kernel<16, W>, grid, block, smem, s, a);
+    return launch_dep(interp2_kernel<8, W>, grid, block, smem, s, a);
   } else {
     switch (lp) {
       case 1: interp_kernel<1, 0, W><<<grid, kInterpThreads, smem, s>>>(a); break;
@@ -898,19 +908,20 @@ cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contr
   if (p.spread_grouped || (p.spread_staged && (p.cs == 8 || p.cs == 16 || p.cs == 32 || p.cs == 64))) {
     dim3 g((unsigned)p.spread_ctas);  // the plan balanced the items over exactly these CTAs
     const size_t smem = spread_stage_smem();
-#define SS(CSV, GR)                                                                                    \
-  spread_stage_kernel<CSV, GR><<<g, kSpreadThreads, smem, s>>>(p.grid, p.contrib, p.sitems, p.sblob, \
-                                                               p.sitem_cta_off, nbins, p.n, p.status_dev)
+#define SS(CSV, GR)                                                                                       \
+  return launch_dep(spread_stage_kernel<CSV, GR>, g, dim3(kSpreadThreads), smem, s, p.grid,                 \
+                    (const float2*)p.contrib, (const int4*)p.sitems, (const int2*)p.sblob,                  \
+                    (const int*)p.sitem_cta_off, nbins, p.n, p.status_dev)
     if (p.spread_grouped) {
       if (p.cs == 32) SS(32, true);
-      else if (p.cs == 64) SS(64, true);
-      else if (p.cs == 16) SS(16, true);
-      else SS(8, true);
+      if (p.cs == 64) SS(64, true);
+      if (p.cs == 16) SS(16, true);
+      SS(8, true);
     } else {
       if (p.cs == 32) SS(32, false);
-      else if (p.cs == 64) SS(64, false);
-      else if (p.cs == 16) SS(16, false);
-      else SS(8, false);
+      if (p.cs == 64) SS(64, false);
+      if (p.cs == 16) SS(16, false);
+      SS(8, false);
     }
 #undef SS
   } else {

@@ -51,6 +51,37 @@ struct DeviceGuard {
   }
 };
 
+// Programmatic dependent launch -------------------------------------------
+//
+// The kernels of the iteration chain (column FFTs, interpolation, spread,
+// fused row kernel) are launched with programmatic stream serialisation: a
+// kernel may be scheduled onto SMs that its predecessor on the stream has
+// already left, and runs the part of its prologue that reads only plan
+// tables (barrier set-up, twiddles, staged spread lists) before the
+// predecessor has finished.  Every thread of such a kernel calls
+// grid_dep_wait() before it reads or writes any buffer that an earlier
+// kernel of the stream may touch; grid_dep_wait() returns once the
+// predecessor grid has completed and its memory operations are visible.
+// grid_dep_release() then lets the successor be scheduled in turn.  For a
+// kernel launched without the attribute both are no-ops.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... P, class... A>
+cudaError_t launch_dep(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 // Deterministic "last block reduces" accumulator: every block writes one
 // double partial, the block that arrives last sums them in index order.
 struct Reducer {

@@ -92,6 +92,13 @@ typedef struct prop_plan_desc {
                              accurate operator, 64 instead of 36 taps per sample) */
   int bin_chunk;          /* bins per oversampled-grid pass: 0 = auto (min(Nf, 64)), else 1..64.
                              Smaller chunks recompute the grid per chunk in less memory. */
+  int row_kernel;         /* row kernel of prop_reconstruct / prop_recon_step (single bin chunk):
+                             0 = auto, 1 = one CTA per (image row, 16 bins),
+                             2 = persistent warp-specialised (the update of one row overlaps
+                             the row FFTs of its neighbours; needs 2N <= 512, 2N != 16 and a bin
+                             stride that is a multiple of 16, else plan creation fails).
+                             Auto takes 2 when it is possible and there are at least 8
+                             (row, 16-bin) units per SM, else 1.  Same iterates either way. */
   int device;             /* CUDA device ordinal */
 } prop_plan_desc;
 

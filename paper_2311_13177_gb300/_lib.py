@@ -27,7 +27,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("n", c_int), ("nf", c_int), ("delta", ctypes.POINTER(c_double)),
                 ("nblades", c_int), ("theta", ctypes.POINTER(c_double)), ("lines", c_int),
                 ("readout", c_int), ("nframes", c_int), ("blade_frame", ctypes.POINTER(c_int)),
-                ("kb_width", c_int), ("bin_chunk", c_int), ("device", c_int)]
+                ("kb_width", c_int), ("bin_chunk", c_int), ("row_kernel", c_int),
+                ("device", c_int)]
 
 
 class ReconParamsC(ctypes.Structure):

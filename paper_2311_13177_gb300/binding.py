@@ -59,7 +59,8 @@ def _dev_ptr(t: torch.Tensor, shape, name: str) -> ctypes.c_void_p:
 class Plan:
     """A libprop plan (geometry tables + workspace on one device)."""
 
-    def __init__(self, N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None, kb_width=0):
+    def __init__(self, N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None, kb_width=0,
+                 row_kernel=0):
         theta = np.ascontiguousarray(theta, dtype=np.float64)
         delta = np.ascontiguousarray(delta, dtype=np.float64)
         if device is None:
@@ -73,7 +74,7 @@ class Plan:
             bf_ptr = self._bf.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         desc = PlanDesc(self.N, self.Nf, delta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         self.B, theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.L, self.R,
-                        self.T, bf_ptr, int(kb_width), int(bin_chunk), int(device))
+                        self.T, bf_ptr, int(kb_width), int(bin_chunk), int(row_kernel), int(device))
         h = ctypes.c_void_p()
         check(lib().prop_plan_create(ctypes.byref(desc), ctypes.byref(h)), "prop_plan_create")
         self._h = h
@@ -216,8 +217,9 @@ def _host_ptr(a, shape, name) -> ctypes.c_void_p:
 
 
 # Function-style aliases with the C ABI's names.
-def prop_plan_create(N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None, kb_width=0) -> Plan:
-    return Plan(N, L, R, theta, delta, blade_frame, T, bin_chunk, device, kb_width)
+def prop_plan_create(N, L, R, theta, delta, blade_frame=None, T=1, bin_chunk=0, device=None, kb_width=0,
+                     row_kernel=0) -> Plan:
+    return Plan(N, L, R, theta, delta, blade_frame, T, bin_chunk, device, kb_width, row_kernel)
 
 
 def prop_plan_destroy(plan: Plan) -> None:

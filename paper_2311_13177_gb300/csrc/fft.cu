@@ -234,10 +234,21 @@ struct NoHook {
   __device__ void operator()() const {}
 };
 
+// Barrier between passes: the whole CTA, or a named barrier over the first
+// COUNT threads when only part of the CTA transforms.
+struct CtaSync {
+  __device__ static void sync() { __syncthreads(); }
+};
+template <int ID, int COUNT>
+struct GroupSync {
+  static_assert(COUNT % 32 == 0, "named barriers count whole warps");
+  __device__ static void sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory"); }
+};
+
 // `hook` runs once, on every thread, right after the barrier that follows
 // the first pass (all reads of the first pass's input are then complete).
-template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class In, class Out,
-          class Hook = NoHook>
+template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class Sync = CtaSync, class In,
+          class Out, class Hook = NoHook>
 __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, int tl, const In& in,
                                          const Out& out, const Hook& hook = Hook()) {
   constexpr RadixPlan RP = radix_plan(NFFT);
@@ -297,7 +308,7 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
     Dft<R, SIGN>::run(v + q * R);
   }
   if constexpr (!LAST) {
-    if constexpr (!FIRST) __syncthreads();  // every read of this pass is done
+    if constexpr (!FIRST) Sync::sync();  // every read of this pass is done
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int j = tl + TPL * q;
@@ -305,9 +316,9 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
 #pragma unroll
       for (int r = 0; r < R; ++r) X[(d + r * NS) * kFftCols + col] = v[q * R + r];
     }
-    __syncthreads();
+    Sync::sync();
     if constexpr (FIRST) hook();
-    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT>(X, tws, col, tl, in, out, hook);
+    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT, Sync>(X, tws, col, tl, in, out, hook);
   } else {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -498,6 +509,11 @@ struct FusedArgs {
   int N, n, Nf, C, T;
   float scale;         // adjoint scale (1/N)
   AdamArgs ad;
+  // warp-specialised kernel only
+  int* err;            // device status word (bounded wait expired)
+  int units;           // (t, i2, 16-bin) row units, unit = (t N + i2) nfb + bin group
+  int nfb;             // 16-bin groups per image row
+  int bh, nbox;        // tensor-copy box height and boxes per unit
 };
 
 // Adjoint output into the CTA's gradient buffer gb[i1][col].
@@ -521,6 +537,94 @@ struct InNewRow {
   __device__ float2 at(int i1, int col) const { return cscale_rn(vb[i1 * kFftCols + col], dp[i1] * c2); }
 };
 
+// TV + Adam on the (t, i2) image row, bins fbase .. fbase + 15, voxels
+// e = e0, e0 + stride, ... of the [N][16] slice: the adjoint gradient comes
+// from gb[e], the new value goes to Vout and back into gb[e] (zero for bins
+// >= Nf, the padding of the next forward row transform).  Adds this thread's
+// TV shares to `local` in voxel order and returns it.  Every load is
+// unconditional (missing neighbours and bins >= Nf read a valid voxel whose
+// value is then not used), so the loads of several voxels are in flight
+// together; TT: the volume has time neighbours (T > 1 and tv_t != 0).
+template <bool TT>
+__device__ __forceinline__ float update_row(const FusedArgs& a, float2* gb, size_t row, int i2, int t, int fbase,
+                                            int e0, int stride, float local) {
+  const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
+  // The volumes and moments never alias: loads of later voxels may be issued
+  // ahead of the stores of earlier ones.
+  const float2* __restrict__ Vin = a.Vin;
+  float2* __restrict__ Vout = a.Vout;
+  float2* __restrict__ mom1 = a.m;
+  float2* __restrict__ mom2 = a.v;
+  const size_t sx = (size_t)a.Nf, sy = (size_t)a.N * a.Nf, st = (size_t)a.N * a.N * a.Nf;
+  const bool xy = a.ad.tv_xy != 0.f;
+  const bool h2p = xy && i2 + 1 < a.N, h2m = xy && i2 > 0;
+  const bool htp = TT && t + 1 < a.T, htm = TT && t > 0;
+#pragma unroll 4
+  for (int e = e0; e < a.N * kFftCols; e += stride) {
+    const int i1 = e / kFftCols;
+    const int f = fbase + (e % kFftCols);
+    const bool fv = f < a.Nf;
+    const size_t idx = (row * a.N + i1) * a.Nf + (fv ? f : a.Nf - 1);
+    TvNbrs nb;
+    nb.h1p = xy && i1 + 1 < a.N;
+    nb.h1m = xy && i1 > 0;
+    nb.h2p = h2p;
+    nb.h2m = h2m;
+    nb.htp = htp;
+    nb.htm = htm;
+    const float2 x = Vin[idx];
+    nb.x1p = Vin[nb.h1p ? idx + sx : idx];
+    nb.x1m = Vin[nb.h1m ? idx - sx : idx];
+    nb.x2p = Vin[h2p ? idx + sy : idx];
+    nb.x2m = Vin[h2m ? idx - sy : idx];
+    if constexpr (TT) {
+      nb.tp = Vin[htp ? idx + st : idx];
+      nb.tm = Vin[htm ? idx - st : idx];
+    } else {
+      nb.tp = nb.tm = x;
+    }
+    float2 mm = mom1[idx], vv = mom2[idx];
+    const float2 gd = gb[e];
+    float2 gxy, gt;
+    const float tv = voxel_tv_nb(x, nb, a.ad.tv_xy, TT ? a.ad.tv_t : 0.f, eps2, &gxy, &gt);
+    float2 nx = make_float2(0.f, 0.f);
+    if (fv) {
+      local = __fadd_rn(local, tv);
+      const float2 g = total_grad(gd, gxy, gt, a.ad);
+      nx = adam_voxel(x, g, mm, vv, a.ad);
+      mom1[idx] = mm;
+      mom2[idx] = vv;
+      Vout[idx] = nx;
+    }
+    gb[e] = nx;
+  }
+  return local;
+}
+
+__device__ __forceinline__ float update_row_any(const FusedArgs& a, float2* gb, size_t row, int i2, int t,
+                                                int fbase, int e0, int stride, float local) {
+  if (a.T > 1 && a.ad.tv_t != 0.f) return update_row<true>(a, gb, row, i2, t, fbase, e0, stride, local);
+  return update_row<false>(a, gb, row, i2, t, fbase, e0, stride, local);
+}
+
+// L2 prefetch of the update's operands for image row `row`: this row of V,
+// m and v, and the neighbouring rows the TV terms read.
+__device__ __forceinline__ void prefetch_update_rows(const FusedArgs& a, size_t row, int i2, int t) {
+  const size_t rl = (size_t)a.N * a.Nf;
+  const uint32_t rb = (uint32_t)(rl * sizeof(float2));
+  prefetch_l2(a.Vin + row * rl, rb);
+  prefetch_l2(a.m + row * rl, rb);
+  prefetch_l2(a.v + row * rl, rb);
+  if (a.ad.tv_xy != 0.f) {
+    if (i2 + 1 < a.N) prefetch_l2(a.Vin + (row + 1) * rl, rb);
+    if (i2 > 0) prefetch_l2(a.Vin + (row - 1) * rl, rb);
+  }
+  if (a.ad.tv_t != 0.f) {
+    if (t + 1 < a.T) prefetch_l2(a.Vin + (row + a.N) * rl, rb);
+    if (t > 0) prefetch_l2(a.Vin + (row - a.N) * rl, rb);
+  }
+}
+
 // Register cap: 64 a thread (two CTAs of 512 threads per SM).
 template <int NFFT>
 constexpr int fused_min_blocks() {
@@ -543,23 +647,8 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_
   build_twiddles<NFFT>(tw, a.twiddle);
   grid_dep_wait();
   grid_dep_release();
-  if (threadIdx.x == 0) {
-    // the update's operands stream into L2 while the inverse FFT runs: this
-    // image row of V, m and v, and the neighbouring rows the TV terms read
-    const size_t rl = (size_t)a.N * a.Nf;
-    const uint32_t rb = (uint32_t)(rl * sizeof(float2));
-    prefetch_l2(a.Vin + row * rl, rb);
-    prefetch_l2(a.m + row * rl, rb);
-    prefetch_l2(a.v + row * rl, rb);
-    if (a.ad.tv_xy != 0.f) {
-      if (i2 + 1 < a.N) prefetch_l2(a.Vin + (row + 1) * rl, rb);
-      if (i2 > 0) prefetch_l2(a.Vin + (row - 1) * rl, rb);
-    }
-    if (a.ad.tv_t != 0.f) {
-      if (t + 1 < a.T) prefetch_l2(a.Vin + (row + a.N) * rl, rb);
-      if (t > 0) prefetch_l2(a.Vin + (row - a.N) * rl, rb);
-    }
-  }
+  // the update's operands stream into L2 while the inverse FFT runs
+  if (threadIdx.x == 0) prefetch_update_rows(a, row, i2, t);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
@@ -570,34 +659,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_
     fft_pass<NFFT, EV, +1, 0, 1, false, true>(X, tw, col, tl, in, out);
   }
   __syncthreads();
-  const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
-  float local = 0.f;
-  // The volumes and moments never alias: loads of later voxels may be issued
-  // ahead of the stores of earlier ones.
-  const float2* __restrict__ Vin = a.Vin;
-  float2* __restrict__ Vout = a.Vout;
-  float2* __restrict__ mom1 = a.m;
-  float2* __restrict__ mom2 = a.v;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < a.N * kFftCols; e += blockDim.x) {
-    const int i1 = e / kFftCols;
-    const int f = fbase + (e % kFftCols);
-    float2 nx = make_float2(0.f, 0.f);
-    if (f < a.Nf) {
-      const size_t idx = (row * a.N + i1) * a.Nf + f;
-      const float2 x = Vin[idx];
-      float2 gxy, gt;
-      local = __fadd_rn(local, voxel_tv(Vin, idx, x, i1, i2, t, a.N, a.Nf, a.T, a.ad.tv_xy, a.ad.tv_t, eps2,
-                                        &gxy, &gt));
-      const float2 g = total_grad(gb[e], gxy, gt, a.ad);
-      float2 mm = mom1[idx], vv = mom2[idx];
-      nx = adam_voxel(x, g, mm, vv, a.ad);
-      mom1[idx] = mm;
-      mom2[idx] = vv;
-      Vout[idx] = nx;
-    }
-    gb[e] = nx;
-  }
+  const float local = update_row_any(a, gb, row, i2, t, fbase, threadIdx.x, blockDim.x, 0.f);
   if constexpr (FWD_TAIL) {
     __syncthreads();
     InNewRow in{gb, a.deapod, a.N, a.n, a.deapod[i2]};
@@ -620,6 +682,175 @@ cudaError_t launch_fused(const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStrea
   return launch_dep(fused_rows_kernel<NFFT, false>, grid, block, smem, s, a);
 }
 
+// --- Warp-specialised fused row kernel ---------------------------------------
+//
+// Persistent CTAs (one per SM) walk the row units u = blockIdx.x + i
+// gridDim.x.  The first FT threads (the transform group, one FFT tile's
+// worth) run, for i = 0, 1, ...: the inverse row FFT of unit i into
+// gradient buffer i % 2, then the forward row FFT of unit i - 1 from buffer
+// (i - 1) % 2; the other kUpdThreads threads (the update group) meanwhile
+// apply TV + Adam to unit i - 1 .. i in place in its buffer.  The update's
+// HBM stream of V, m and v thus overlaps the transforms' shared-memory work
+// instead of following it.  The adjoint input of unit i + 1 is staged by a
+// tensor copy as soon as the first pass of unit i has read the stage.
+// Hand-offs: ready[b] (every transform thread arrives once the inverse FFT
+// has written buffer b) and done[b] (every update thread arrives once it
+// has rewritten buffer b); each group synchronises internally on its own
+// named barrier.  A group gives up on an expired bounded wait (the status
+// word is set); the other group's next wait then expires too.  The
+// arithmetic is that of fused_rows_kernel, so the iterates agree bit for
+// bit; the TV partial sums are per CTA.
+constexpr int kUpdThreads = 512;
+
+// Input staged in shared memory as [rows][kFftCols].
+struct InTile {
+  const float2* t;  // [rows][kFftCols]
+  __device__ float2 at(int i, int col) const { return t[i * kFftCols + col]; }
+  __device__ float2 operator()(int pos, int col) const { return t[pos * kFftCols + col]; }
+};
+
+template <int NFFT>
+constexpr bool fused_ws_fits() {
+  return Shape<NFFT, kValsFused<NFFT>>::THREADS % 32 == 0 && Shape<NFFT, kValsFused<NFFT>>::THREADS <= 512;
+}
+
+template <int NFFT>
+constexpr size_t fused_ws_smem() {
+  // stage + transform workspace [NFFT][16], two gradient buffers [N][16], twiddles, 5 mbarriers
+  return (size_t)2 * NFFT * kFftCols * sizeof(float2) + (size_t)2 * (NFFT / 2) * kFftCols * sizeof(float2) +
+         (size_t)Shape<NFFT, kValsFused<NFFT>>::TW * sizeof(float2) + 5 * sizeof(uint64_t);
+}
+
+template <int NFFT, bool FWD_TAIL>
+__global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS + kUpdThreads, 1)
+    fused_rows_ws_kernel(const __grid_constant__ CUtensorMap tin, FusedArgs a) {
+  constexpr int EV = kValsFused<NFFT>;
+  constexpr int FT = Shape<NFFT, EV>::THREADS;
+  using FSync = GroupSync<1, FT>;
+  using USync = GroupSync<2, kUpdThreads>;
+  extern __shared__ __align__(128) float2 smem[];
+  float2* S = smem;                          // [NFFT][16] staged adjoint input
+  float2* X = S + NFFT * kFftCols;           // [NFFT][16] transform workspace
+  float2* gbuf = X + NFFT * kFftCols;        // [2][N][16]
+  float2* tw = gbuf + 2 * (NFFT / 2) * kFftCols;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tw + Shape<NFFT, EV>::TW);
+  uint64_t* ready = full + 1;                // [2]
+  uint64_t* done = full + 3;                 // [2]
+  __shared__ volatile int s_abort_f, s_abort_u;
+  const int nu = (int)blockIdx.x < a.units ? (a.units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int gsz = a.N * kFftCols;
+  const uint32_t tile_bytes = (uint32_t)(NFFT * kFftCols * sizeof(float2));
+  auto issue = [&](int i) {
+    const int u = (int)blockIdx.x + i * (int)gridDim.x;
+    const int row = u / a.nfb, fb = u - (u / a.nfb) * a.nfb;
+    mbar_expect_tx(full, tile_bytes);
+    for (int b = 0; b < a.nbox; ++b)
+      tma_load_3d(S + (size_t)b * a.bh * kFftCols, &tin, fb * 2 * kFftCols, b * a.bh, row, full);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ready[b], FT);
+      mbar_init(&done[b], kUpdThreads);
+    }
+    fence_mbar_init();
+    s_abort_f = 0;
+    s_abort_u = 0;
+  }
+  build_twiddles<NFFT>(tw, a.twiddle);
+  grid_dep_wait();
+  grid_dep_release();
+  int issued = 0, consumed = 0;  // tensor copies, meaningful on thread 0
+  if (threadIdx.x == 0 && nu > 0) {
+    issue(0);
+    issued = 1;
+  }
+  __syncthreads();
+  float local = 0.f;
+  if (threadIdx.x < FT) {
+    const int col = threadIdx.x % kFftCols;
+    const int tl = threadIdx.x / kFftCols;
+    for (int i = 0; i <= nu; ++i) {
+      if (i < nu) {
+        if (!mbar_wait_bounded(full, (uint32_t)(i & 1)))
+          s_abort_f = 1;
+        else
+          ++consumed;
+        FSync::sync();  // the previous forward FFT is done with X; uniform abort flag
+        if (s_abort_f) break;
+        const int u = (int)blockIdx.x + i * (int)gridDim.x;
+        const size_t row = (size_t)(u / a.nfb);
+        const int i2 = (int)(row % a.N);
+        auto hook = [&]() {
+          if (threadIdx.x == 0 && i + 1 < nu) {
+            fence_proxy_async_smem();
+            issue(i + 1);
+            ++issued;
+          }
+        };
+        InTile in{S};
+        OutGrad out{gbuf + (size_t)(i & 1) * gsz, a.deapod, a.N, a.n, a.deapod[i2] * a.scale};
+        fft_pass<NFFT, EV, +1, 0, 1, false, true, FSync>(X, tw, col, tl, in, out, hook);
+        mbar_arrive(&ready[i & 1]);
+      }
+      if (i >= 1) {
+        const int j = i - 1;
+        if (!mbar_wait_bounded(&done[j & 1], (uint32_t)((j >> 1) & 1))) s_abort_f = 1;
+        FSync::sync();  // the inverse FFT's last pass is done with X; uniform abort flag
+        if (s_abort_f) break;
+        if constexpr (FWD_TAIL) {
+          const int u = (int)blockIdx.x + j * (int)gridDim.x;
+          const size_t row = (size_t)(u / a.nfb);
+          const int fbase = (u - (u / a.nfb) * a.nfb) * kFftCols;
+          const int i2 = (int)(row % a.N);
+          InNewRow in{gbuf + (size_t)(j & 1) * gsz, a.deapod, a.N, a.n, a.deapod[i2]};
+          OutFwdRows out{a.rows, a.n, a.C, fbase, row};
+          fft_pass<NFFT, EV, -1, 0, 1, true, false, FSync>(X, tw, col, tl, in, out);
+        }
+      }
+    }
+  } else {
+    const int ut = threadIdx.x - FT;
+    if (ut == 0 && nu > 0) {
+      const size_t row = (size_t)(blockIdx.x / a.nfb);
+      prefetch_update_rows(a, row, (int)(row % a.N), (int)(row / a.N));
+    }
+    for (int i = 0; i < nu; ++i) {
+      const int u = (int)blockIdx.x + i * (int)gridDim.x;
+      const size_t row = (size_t)(u / a.nfb);
+      const int fbase = (u - (u / a.nfb) * a.nfb) * kFftCols;
+      const int i2 = (int)(row % a.N), t = (int)(row / a.N);
+      if (ut == 0 && i + 1 < nu) {
+        const size_t nrow = (size_t)((u + (int)gridDim.x) / a.nfb);
+        if (nrow != row) prefetch_update_rows(a, nrow, (int)(nrow % a.N), (int)(nrow / a.N));
+      }
+      if (!mbar_wait_bounded(&ready[i & 1], (uint32_t)((i >> 1) & 1))) s_abort_u = 1;
+      USync::sync();
+      if (s_abort_u) break;
+      local = update_row_any(a, gbuf + (size_t)(i & 1) * gsz, row, i2, t, fbase, ut, kUpdThreads, local);
+      mbar_arrive(&done[i & 1]);
+    }
+  }
+  __syncthreads();
+  if ((s_abort_f || s_abort_u) && threadIdx.x == 0) {
+    atomicExch(a.err, 1);
+    // let copies issued and never awaited land (bounded)
+    for (int k = consumed; k < issued; ++k) mbar_wait_bounded(full, (uint32_t)(k & 1));
+  }
+  finish_loss(local, a.partials, a.counter, a.data_loss, a.loss_out);
+}
+
+template <int NFFT>
+cudaError_t launch_fused_ws(const CUtensorMap& tm, const FusedArgs& a, bool fwd_tail, int ctas, cudaStream_t s) {
+  if constexpr (fused_ws_fits<NFFT>()) {
+    const dim3 grid((unsigned)ctas), block(Shape<NFFT, kValsFused<NFFT>>::THREADS + kUpdThreads);
+    if (fwd_tail) return launch_dep(fused_rows_ws_kernel<NFFT, true>, grid, block, fused_ws_smem<NFFT>(), s, tm, a);
+    return launch_dep(fused_rows_ws_kernel<NFFT, false>, grid, block, fused_ws_smem<NFFT>(), s, tm, a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
 // --- Column passes staged by TMA ------------------------------------------
 //
 // Persistent CTAs walk the column tiles (16 adjacent (u1, bin) lines of one
@@ -628,12 +859,6 @@ cudaError_t launch_fused(const FusedArgs& a, bool fwd_tail, dim3 grid, cudaStrea
 // tiles streams in while this one is transformed.
 // Forward: the staged input is the N image rows of the row intermediate
 // (padding is never stored); adjoint: the 2N grid rows.
-struct InTile {
-  const float2* t;  // [rows][kFftCols]
-  __device__ float2 at(int i, int col) const { return t[i * kFftCols + col]; }
-  __device__ float2 operator()(int pos, int col) const { return t[pos * kFftCols + col]; }
-};
-
 struct ColArgs {
   float2* dst;
   const float2* twiddle;
@@ -765,7 +990,20 @@ cudaError_t configure_n() {
   const int fsm = (int)fused_smem<NFFT>(NFFT / 2);
   if ((e = cudaFuncSetAttribute(fused_rows_kernel<NFFT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
     return e;
-  return cudaFuncSetAttribute(fused_rows_kernel<NFFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+  if ((e = cudaFuncSetAttribute(fused_rows_kernel<NFFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
+    return e;
+  if constexpr (fused_ws_fits<NFFT>()) {
+    if (fused_ws_smem<NFFT>() <= (size_t)optin - 1024) {
+      const int wsm = (int)fused_ws_smem<NFFT>();
+      if ((e = cudaFuncSetAttribute(fused_rows_ws_kernel<NFFT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    wsm)))
+        return e;
+      if ((e = cudaFuncSetAttribute(fused_rows_ws_kernel<NFFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    wsm)))
+        return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 #define PROP_FFT_SIZES(X) X(16) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
@@ -842,6 +1080,27 @@ cudaError_t dispatch_fused(int n, const FusedArgs& a, bool fwd_tail, dim3 grid, 
   }
 }
 
+cudaError_t dispatch_fused_ws(int n, const CUtensorMap& tm, const FusedArgs& a, bool fwd_tail, int ctas,
+                              cudaStream_t s) {
+  switch (n) {
+#define CASE(v) \
+  case v: return launch_fused_ws<v>(tm, a, fwd_tail, ctas, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool fused_ws_size_ok(int n, size_t room) {
+  switch (n) {
+#define CASE(v) \
+  case v: return fused_ws_fits<v>() && fused_ws_smem<v>() <= room;
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return false;
+  }
+}
+
 FftArgs base_args(const Plan& p) {
   FftArgs a{};
   a.deapod = p.deapod;
@@ -909,6 +1168,24 @@ void fft_make_maps(Plan& p) {
   const size_t room = (size_t)p.smem_optin - 1024;
   p.cols_tma_fwd = cols_smem(p.n, kFwdCols) <= room && make(&p.tm_rows, p.rows, p.N);
   p.cols_tma_adj = cols_smem(p.n, kAdjCols) <= room && make(&p.tm_grid, p.grid, p.n);
+  // fused row kernel input: [T N][n][2 cs] floats, box = 16 bins x box_rows(n) positions of one row.
+  // Automatic choice: the warp-specialised kernel pipelines the units of a
+  // CTA, which pays off once every SM has several (at 3.4 units per SM the
+  // per-row CTAs were faster, at 27 the warp-specialised kernel by a fifth).
+  p.fused_ws = false;
+  const long units = (long)((p.Nf + kFftCols - 1) / kFftCols) * p.T * p.N;
+  const bool want = p.row_kernel == 2 || (p.row_kernel == 0 && units >= 8L * p.num_sms);
+  if (want && p.cs % kFftCols == 0 && p.nchunks == 1 && (size_t)p.T * p.N <= 0xffffffffu &&
+      fused_ws_size_ok(p.n, room)) {
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * p.cs), (cuuint64_t)p.n, (cuuint64_t)p.T * p.N};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * p.cs * sizeof(float)),
+                                   (cuuint64_t)(2 * (size_t)p.cs * p.n * sizeof(float))};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * kFftCols), (cuuint32_t)box_rows(p.n), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    p.fused_ws = encode(&p.tm_fused, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p.rows, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
 }
 
 cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s) {
@@ -963,6 +1240,16 @@ cudaError_t fused_rows_update(const Plan& p, const float2* Vin, float2* m, float
   a.T = p.T;
   a.scale = 1.0f / (float)p.N;
   a.ad = aa;
+  a.err = p.status_dev;
+  a.nfb = (p.Nf + kFftCols - 1) / kFftCols;
+  a.units = a.nfb * p.T * p.N;
+  if (p.fused_ws) {
+    a.bh = box_rows(p.n);
+    a.nbox = p.n / a.bh;
+    const int ctas = std::max(1, std::min(a.units, p.num_sms));
+    if (ctas > red->capacity) return cudaErrorInvalidValue;
+    return dispatch_fused_ws(p.n, p.tm_fused, a, fwd_tail, ctas, s);
+  }
   dim3 grid((p.Nf + kFftCols - 1) / kFftCols, p.T * p.N);
   if ((long)grid.x * grid.y > red->capacity) return cudaErrorInvalidValue;
   return dispatch_fused(p.n, a, fwd_tail, grid, s);

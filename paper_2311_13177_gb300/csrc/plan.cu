@@ -239,6 +239,8 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
     return fail(PROP_ERR_INVALID_ARG, "plan_create: kb_width must be 0 (= 6), 6 or 8");
   if (d->bin_chunk < 0 || d->bin_chunk > kMaxChunk)
     return fail(PROP_ERR_INVALID_ARG, "plan_create: bin_chunk must be in [0, 64]");
+  if (d->row_kernel < 0 || d->row_kernel > 2)
+    return fail(PROP_ERR_INVALID_ARG, "plan_create: row_kernel must be 0, 1 or 2");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
     cudaGetLastError();
@@ -629,7 +631,14 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   TRY(upload(p->sblob, blob));
   if (!items.empty()) TRY(upload(p->items, items));
   TRY(upload(p->item_cta_off, cta_off));
+  p->row_kernel = d->row_kernel;
   fft_make_maps(*p);
+  if (p->row_kernel == 2 && !p->fused_ws) {
+    plan_free(p);
+    return fail(PROP_ERR_INVALID_ARG,
+                "plan_create: row_kernel 2 needs 2N <= 512, 2N != 16, one bin chunk and a bin stride that is a "
+                "multiple of 16");
+  }
   {
     cudaError_t e = fft_configure(n);
     // The interpolation may use the device's whole opt-in shared memory.

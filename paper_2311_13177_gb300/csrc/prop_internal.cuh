@@ -145,6 +145,12 @@ struct Plan {
   CUtensorMap tm_rows;
   CUtensorMap tm_grid;
   bool cols_tma_fwd = false, cols_tma_adj = false;
+  // Row workspace seen as [T N][n][2 cs floats]: a box is the 16-bin slice
+  // of one image row's n positions, the input of the warp-specialised fused
+  // row kernel (used when its size and bin stride allow)
+  CUtensorMap tm_fused;
+  bool fused_ws = false;         // the warp-specialised row kernel runs (row_kernel rule below)
+  int row_kernel = 0;            // as requested: 0 auto, 1 per-row CTAs, 2 warp-specialised
 
   // grid workspace (one bin chunk)
   float2* grid = nullptr;        // [T][n][n][chunk]

@@ -26,38 +26,67 @@ __device__ __forceinline__ float2 cadd_rn(float2 a, float2 b) {
   return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
 }
 
-// TV gradients at voxel idx = ((t N + i2) N + i1) Nf + f of Vin (value x):
-// forward differences along x1, x2 and t, no wrap-around.  *gxy, *gt get the
-// gradients of TV_xy and TV_t; the return value is this voxel's own share of
-// the weighted TV value (the terms of the differences it is the lower end of).
-__device__ __forceinline__ float voxel_tv(const float2* __restrict__ Vin, size_t idx, float2 x, int i1, int i2,
-                                          int t, int N, int Nf, int T, float tv_xy, float tv_t, float eps2,
-                                          float2* gxy_out, float2* gt_out) {
-  const size_t sx = (size_t)Nf, sy = (size_t)N * Nf, st = (size_t)N * N * Nf;
+// The six neighbours of a voxel along x1, x2 and t (+ and -) and which of
+// them exist: differences that would reach outside the volume are left out
+// (no wrap-around).
+struct TvNbrs {
+  float2 x1p, x1m, x2p, x2m, tp, tm;
+  bool h1p, h1m, h2p, h2m, htp, htm;
+};
+
+// TV gradients at a voxel of value x from its neighbours: forward
+// differences along x1, x2 and t.  *gxy, *gt get the gradients of TV_xy and
+// TV_t; the return value is this voxel's own share of the weighted TV value
+// (the terms of the differences it is the lower end of).
+__device__ __forceinline__ float voxel_tv_nb(float2 x, const TvNbrs& nb, float tv_xy, float tv_t, float eps2,
+                                             float2* gxy_out, float2* gt_out) {
   float2 gxy = make_float2(0.f, 0.f), gt = make_float2(0.f, 0.f);
   float mag, sxy = 0.f, stt = 0.f;
   if (tv_xy != 0.f) {
-    if (i1 + 1 < N) {
-      gxy = csub_rn(gxy, tv_term(csub_rn(Vin[idx + sx], x), eps2, &mag));
+    if (nb.h1p) {
+      gxy = csub_rn(gxy, tv_term(csub_rn(nb.x1p, x), eps2, &mag));
       sxy = __fadd_rn(sxy, mag);
     }
-    if (i1 > 0) gxy = cadd_rn(gxy, tv_term(csub_rn(x, Vin[idx - sx]), eps2, &mag));
-    if (i2 + 1 < N) {
-      gxy = csub_rn(gxy, tv_term(csub_rn(Vin[idx + sy], x), eps2, &mag));
+    if (nb.h1m) gxy = cadd_rn(gxy, tv_term(csub_rn(x, nb.x1m), eps2, &mag));
+    if (nb.h2p) {
+      gxy = csub_rn(gxy, tv_term(csub_rn(nb.x2p, x), eps2, &mag));
       sxy = __fadd_rn(sxy, mag);
     }
-    if (i2 > 0) gxy = cadd_rn(gxy, tv_term(csub_rn(x, Vin[idx - sy]), eps2, &mag));
+    if (nb.h2m) gxy = cadd_rn(gxy, tv_term(csub_rn(x, nb.x2m), eps2, &mag));
   }
   if (tv_t != 0.f) {
-    if (t + 1 < T) {
-      gt = csub_rn(gt, tv_term(csub_rn(Vin[idx + st], x), eps2, &mag));
+    if (nb.htp) {
+      gt = csub_rn(gt, tv_term(csub_rn(nb.tp, x), eps2, &mag));
       stt = __fadd_rn(stt, mag);
     }
-    if (t > 0) gt = cadd_rn(gt, tv_term(csub_rn(x, Vin[idx - st]), eps2, &mag));
+    if (nb.htm) gt = cadd_rn(gt, tv_term(csub_rn(x, nb.tm), eps2, &mag));
   }
   *gxy_out = gxy;
   *gt_out = gt;
   return fmaf(tv_xy, sxy, __fmul_rn(tv_t, stt));
+}
+
+// voxel_tv_nb at voxel idx = ((t N + i2) N + i1) Nf + f of Vin (value x),
+// loading the neighbours that exist.
+__device__ __forceinline__ float voxel_tv(const float2* __restrict__ Vin, size_t idx, float2 x, int i1, int i2,
+                                          int t, int N, int Nf, int T, float tv_xy, float tv_t, float eps2,
+                                          float2* gxy_out, float2* gt_out) {
+  const size_t sx = (size_t)Nf, sy = (size_t)N * Nf, st = (size_t)N * N * Nf;
+  const float2 z = make_float2(0.f, 0.f);
+  TvNbrs nb;
+  nb.h1p = tv_xy != 0.f && i1 + 1 < N;
+  nb.h1m = tv_xy != 0.f && i1 > 0;
+  nb.h2p = tv_xy != 0.f && i2 + 1 < N;
+  nb.h2m = tv_xy != 0.f && i2 > 0;
+  nb.htp = tv_t != 0.f && t + 1 < T;
+  nb.htm = tv_t != 0.f && t > 0;
+  nb.x1p = nb.h1p ? Vin[idx + sx] : z;
+  nb.x1m = nb.h1m ? Vin[idx - sx] : z;
+  nb.x2p = nb.h2p ? Vin[idx + sy] : z;
+  nb.x2m = nb.h2m ? Vin[idx - sy] : z;
+  nb.tp = nb.htp ? Vin[idx + st] : z;
+  nb.tm = nb.htm ? Vin[idx - st] : z;
+  return voxel_tv_nb(x, nb, tv_xy, tv_t, eps2, gxy_out, gt_out);
 }
 
 // g = gscale * gd + tv_xy * gxy + tv_t * gt

@@ -27,7 +27,7 @@ def plan_desc(N, L, R, theta, delta, blade_frame=None, T=1, kb_width=0, bin_chun
         bf = frames.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     d = PlanDesc(int(N), len(delta), delta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(theta),
                  theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(L), int(R), int(T), bf,
-                 int(kb_width), int(bin_chunk), 0)
+                 int(kb_width), int(bin_chunk), 0, 0)
     return d, keep
 
 

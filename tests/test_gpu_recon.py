@@ -110,3 +110,62 @@ def test_host_api_matches_device_api():
     plan.destroy()
     assert rel(Vh, Vd.cpu().numpy()) < 1e-6
     assert np.allclose(trh, trd, rtol=1e-6)
+
+
+def _row_kernel_plan(c, T, row_kernel):
+    from paper_2311_13177_gb300 import Plan
+    return Plan(c["N"], c["L"], c["R"], c["theta"], c["delta"], c["blade_frame"], T, kb_width=8,
+                row_kernel=row_kernel)
+
+
+def test_row_kernels_same_iterates_and_match_oracle():
+    """row_kernel 1 (one CTA per image row and 16 bins) and 2 (persistent,
+    warp-specialised): the same iterates bit for bit, both within the
+    reconstruction bar of the oracle.  Two frames (temporal TV), 16 bins."""
+    from paper_2311_13177_gb300 import ReconParams
+    c = random_case(32, 16, 4, 6, 32, T=2, seed=21)
+    g = geometry(32, 6, 32, c["theta"], c["delta"], c["blade_frame"], 2)
+    pg = ReconParams(iters=10, lr=1e-2, tv_xy=1e-3, tv_t=1e-2)
+    po = oracle.ReconParams(iters=10, lr=1e-2, tv_xy=1e-3, tv_t=1e-2)
+    y = torch.from_numpy(c["y"]).cuda()
+    out = {}
+    for rk in (1, 2):
+        plan = _row_kernel_plan(c, 2, rk)
+        out[rk] = plan.reconstruct(y, pg)
+        plan.destroy()
+    assert torch.equal(out[1][0], out[2][0])
+    # the TV partial sums are grouped per CTA: the loss traces agree to rounding
+    assert np.max(np.abs(out[1][1] - out[2][1]) / np.abs(out[1][1])) < 1e-6
+    Vo, tro = oracle.reconstruct(c["y"].astype(np.complex128), g, po)
+    assert rel(out[2][0].cpu().numpy(), Vo) < TOL_RECON
+    assert np.max(np.abs(out[2][1] - tro) / np.abs(tro)) < 1e-4
+
+
+def test_warp_specialised_reconstruct_equals_step_sequence():
+    from paper_2311_13177_gb300 import ReconParams
+    c = random_case(48, 31, 5, 6, 48, T=3, seed=22)   # 2N = 96 (radix 3), ragged second bin group
+    pg = ReconParams(iters=6, lr=1e-2, tv_xy=1e-3, tv_t=1e-2)
+    plan = _row_kernel_plan(c, 3, 2)
+    y = torch.from_numpy(c["y"]).cuda()
+    V, tr = plan.reconstruct(y, pg)
+    a = torch.zeros(plan.vol_shape, dtype=torch.complex64, device="cuda")
+    b = torch.empty_like(a)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    trs = []
+    for k in range(1, 7):
+        plan.recon_step(y, pg, k, a, b, loss)
+        trs.append(float(loss.item()))
+        a, b = b, a
+    plan.destroy()
+    assert torch.equal(V, a)
+    assert np.array_equal(np.array(trs), tr)
+
+
+@pytest.mark.parametrize("shape", [(8, 16, 2, 4, 8), (32, 8, 3, 4, 32)])
+def test_warp_specialised_row_kernel_rejected_where_impossible(shape):
+    """2N = 16 (a 16-thread transform group) and a bin stride of 8 cannot run it."""
+    from paper_2311_13177_gb300._lib import PropError
+    N, Nf, B, L, R = shape
+    c = random_case(N, Nf, B, L, R, seed=3)
+    with pytest.raises(PropError):
+        _row_kernel_plan(c, 1, 2)

@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--bin-chunk", type=int, default=0, help="bins per grid pass (0: the plan's default)")
+    ap.add_argument("--row-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="row kernel: 0 the plan's choice, 1 per-row CTAs, 2 warp-specialised")
     ap.add_argument("--diff-study", action="store_true",
                     help="differentiation workload: grid store vs recompute (memory and time), one JSON line")
     ap.add_argument("--workload", choices=["static", "dynamic", "diff"], default=WORKLOAD,
@@ -352,7 +354,7 @@ def run_ours(args):
     w_rank = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
     prob = synth.make_problem(w_rank)
     plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=local,
-                bin_chunk=args.bin_chunk)
+                bin_chunk=args.bin_chunk, row_kernel=args.row_kernel)
     params = ReconParams(iters=1, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
     y = torch.from_numpy(prob["y"]).to(dev)
     Va = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)

@@ -537,17 +537,20 @@ struct InNewRow {
   __device__ float2 at(int i1, int col) const { return cscale_rn(vb[i1 * kFftCols + col], dp[i1] * c2); }
 };
 
-// TV + Adam on the (t, i2) image row, bins fbase .. fbase + 15, voxels
-// e = e0, e0 + stride, ... of the [N][16] slice: the adjoint gradient comes
-// from gb[e], the new value goes to Vout and back into gb[e] (zero for bins
-// >= Nf, the padding of the next forward row transform).  Adds this thread's
-// TV shares to `local` in voxel order and returns it.  Every load is
-// unconditional (missing neighbours and bins >= Nf read a valid voxel whose
-// value is then not used), so the loads of several voxels are in flight
-// together; TT: the volume has time neighbours (T > 1 and tv_t != 0).
+// TV + Adam on the (t, i2) image row, bins fbase .. fbase + 15.  The
+// nthreads threads split the row into 16 columns (one bin each) of
+// nthreads / 16 runs of consecutive i1; thread tid walks its run, so the
+// x1 neighbours are the previous and the next voxel of the walk and only the
+// next one is loaded per step.  The adjoint gradient comes from gb[i1][col],
+// the new value goes to Vout and back into gb (zero for bins >= Nf, the
+// padding of the next forward row transform).  Adds this thread's TV shares
+// to `local` in walk order and returns it.  Every load is unconditional
+// (missing neighbours and bins >= Nf read a valid voxel whose value is then
+// not used), so the loads of several steps are in flight together; TT: the
+// volume has time neighbours (T > 1 and tv_t != 0).
 template <bool TT>
 __device__ __forceinline__ float update_row(const FusedArgs& a, float2* gb, size_t row, int i2, int t, int fbase,
-                                            int e0, int stride, float local) {
+                                            int tid, int nthreads, float local) {
   const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
   // The volumes and moments never alias: loads of later voxels may be issued
   // ahead of the stores of earlier ones.
@@ -555,26 +558,35 @@ __device__ __forceinline__ float update_row(const FusedArgs& a, float2* gb, size
   float2* __restrict__ Vout = a.Vout;
   float2* __restrict__ mom1 = a.m;
   float2* __restrict__ mom2 = a.v;
+  const int col = tid % kFftCols;
+  const int runs = nthreads / kFftCols;
+  const int len = (a.N + runs - 1) / runs;
+  const int lo = (tid / kFftCols) * len;
+  const int hi = min(a.N, lo + len);
+  if (lo >= hi) return local;
   const size_t sx = (size_t)a.Nf, sy = (size_t)a.N * a.Nf, st = (size_t)a.N * a.N * a.Nf;
   const bool xy = a.ad.tv_xy != 0.f;
   const bool h2p = xy && i2 + 1 < a.N, h2m = xy && i2 > 0;
   const bool htp = TT && t + 1 < a.T, htm = TT && t > 0;
+  const int f = fbase + col;
+  const bool fv = f < a.Nf;
+  const size_t base = row * a.N * a.Nf + (size_t)(fv ? f : a.Nf - 1);  // voxel (t, i2, 0, f)
+  float2 xm = Vin[lo > 0 ? base + (size_t)(lo - 1) * sx : base];
+  float2 x = Vin[base + (size_t)lo * sx];
 #pragma unroll 4
-  for (int e = e0; e < a.N * kFftCols; e += stride) {
-    const int i1 = e / kFftCols;
-    const int f = fbase + (e % kFftCols);
-    const bool fv = f < a.Nf;
-    const size_t idx = (row * a.N + i1) * a.Nf + (fv ? f : a.Nf - 1);
+  for (int i1 = lo; i1 < hi; ++i1) {
+    const size_t idx = base + (size_t)i1 * sx;
+    const bool more = i1 + 1 < a.N;
+    const float2 xp = Vin[more ? idx + sx : idx];
     TvNbrs nb;
-    nb.h1p = xy && i1 + 1 < a.N;
+    nb.h1p = xy && more;
     nb.h1m = xy && i1 > 0;
     nb.h2p = h2p;
     nb.h2m = h2m;
     nb.htp = htp;
     nb.htm = htm;
-    const float2 x = Vin[idx];
-    nb.x1p = Vin[nb.h1p ? idx + sx : idx];
-    nb.x1m = Vin[nb.h1m ? idx - sx : idx];
+    nb.x1p = xp;
+    nb.x1m = xm;
     nb.x2p = Vin[h2p ? idx + sy : idx];
     nb.x2m = Vin[h2m ? idx - sy : idx];
     if constexpr (TT) {
@@ -584,7 +596,8 @@ __device__ __forceinline__ float update_row(const FusedArgs& a, float2* gb, size
       nb.tp = nb.tm = x;
     }
     float2 mm = mom1[idx], vv = mom2[idx];
-    const float2 gd = gb[e];
+    float2* gp = gb + i1 * kFftCols + col;
+    const float2 gd = *gp;
     float2 gxy, gt;
     const float tv = voxel_tv_nb(x, nb, a.ad.tv_xy, TT ? a.ad.tv_t : 0.f, eps2, &gxy, &gt);
     float2 nx = make_float2(0.f, 0.f);
@@ -596,15 +609,17 @@ __device__ __forceinline__ float update_row(const FusedArgs& a, float2* gb, size
       mom2[idx] = vv;
       Vout[idx] = nx;
     }
-    gb[e] = nx;
+    *gp = nx;
+    xm = x;
+    x = xp;
   }
   return local;
 }
 
 __device__ __forceinline__ float update_row_any(const FusedArgs& a, float2* gb, size_t row, int i2, int t,
-                                                int fbase, int e0, int stride, float local) {
-  if (a.T > 1 && a.ad.tv_t != 0.f) return update_row<true>(a, gb, row, i2, t, fbase, e0, stride, local);
-  return update_row<false>(a, gb, row, i2, t, fbase, e0, stride, local);
+                                                int fbase, int tid, int nthreads, float local) {
+  if (a.T > 1 && a.ad.tv_t != 0.f) return update_row<true>(a, gb, row, i2, t, fbase, tid, nthreads, local);
+  return update_row<false>(a, gb, row, i2, t, fbase, tid, nthreads, local);
 }
 
 // L2 prefetch of the update's operands for image row `row`: this row of V,

@@ -451,7 +451,7 @@ def run_ours(args):
         tr_path = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tr_path):
             with open(tr_path) as f:
-                traffic = json.load(f).get(dom)
+                traffic = json.load(f).get(args.workload, {}).get(dom)
             if traffic is not None:
                 traffic = float(traffic)
         launches = sum(v_[1] for v_ in prof.values())

@@ -283,6 +283,18 @@ PROP_API prop_status prop_profile_read(prop_plan plan, double* ms_out, long long
  * bad device), PROP_ERR_CUDA. */
 PROP_API prop_status prop_fp32_fma_peak(int device, double* tflops);
 
+/* Check of the device-side bounded wait that the staged kernels use
+ * (interpolation, spread, TMA column FFTs, warp-specialised row kernel):
+ * launches one warp that waits on an mbarrier nobody arrives at, bounded by
+ * limit_cycles SM clock cycles (0 < limit_cycles <= 4e9, the kernels' own
+ * bound), and reports *expired = 1 if the wait gave up and the kernel
+ * returned (0 if the phase completed, which cannot happen here).  *ms (may
+ * be NULL) receives the probe's duration.  The device stays usable
+ * afterwards.  Synchronous; allocates and frees 4 bytes of device memory.
+ * Errors: PROP_ERR_INVALID_ARG (null expired, limit out of range, bad
+ * device), PROP_ERR_CUDA. */
+PROP_API prop_status prop_check_bounded_wait(int device, long long limit_cycles, int* expired, double* ms);
+
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 PROP_API const char* prop_last_error(void);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "prop_profile_enable": (c_int, [c_void_p, c_int]),
     "prop_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "prop_fp32_fma_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "prop_check_bounded_wait": (c_int, [c_int, ctypes.c_longlong, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "prop_last_error": (ctypes.c_char_p, []),
 }
 

@@ -281,3 +281,14 @@ def prop_fp32_fma_peak(device: int = None) -> float:
     out = ctypes.c_double()
     check(lib().prop_fp32_fma_peak(int(device), ctypes.byref(out)), "prop_fp32_fma_peak")
     return float(out.value)
+
+
+def prop_check_bounded_wait(limit_cycles: int = 20_000_000, device: int = None):
+    """Runs the bounded-wait probe; returns (expired, milliseconds)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    expired = ctypes.c_int()
+    ms = ctypes.c_double()
+    check(lib().prop_check_bounded_wait(int(device), int(limit_cycles), ctypes.byref(expired), ctypes.byref(ms)),
+          "prop_check_bounded_wait")
+    return int(expired.value), float(ms.value)

@@ -54,12 +54,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2 s of SM clock (no legitimate copy takes
-// that long) and reports false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: gives up after `limit` SM clock cycles (by default 4e9,
+// ~2 s: no legitimate copy or hand-off takes that long) and reports false.
+constexpr long long kWaitLimitCycles = 4000000000LL;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit = kWaitLimitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > 4000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 // Asynchronous prefetch of a contiguous range into L2 (16-byte aligned

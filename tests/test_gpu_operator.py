@@ -150,3 +150,15 @@ def test_fp32_fma_peak_is_plausible():
     tf = prop_fp32_fma_peak(0)
     # 152 SMs x 128 FP32 lanes x 2 flops x ~2 GHz is about 80 TFLOP/s
     assert 10.0 < tf < 200.0, tf
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    """The staged kernels' mbarrier waits are bounded: a wait on a barrier
+    nobody arrives at gives up after its cycle budget, the kernel returns,
+    and the device keeps working."""
+    from paper_2311_13177_gb300.binding import prop_check_bounded_wait
+    expired, ms = prop_check_bounded_wait(20_000_000)   # about 10 ms of SM clock
+    assert expired == 1
+    assert 1.0 < ms < 1000.0, ms
+    x = torch.ones(4096, device="cuda")
+    assert float(x.sum()) == 4096.0

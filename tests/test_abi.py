@@ -56,3 +56,13 @@ def test_estimate_bytes_is_host_only_and_scales(libprop):
     assert 0 < small < big
     # the static workload's grid workspace alone is 67 MB
     assert big > 67e6
+
+
+def test_row_kernel_choice_is_validated_before_any_device_work(libprop):
+    from paper_2311_13177_gb300.serve import plan_desc
+    d, keep = plan_desc(32, 4, 32, [0.0], [0.0])
+    for bad in (-1, 3):
+        d.row_kernel = bad
+        h = ctypes.c_void_p()
+        assert libprop.prop_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1
+        assert b"row_kernel" in libprop.prop_last_error()

@@ -16,6 +16,10 @@ Contents
   recon     data-consistency loss, smoothed TV in x-y and in time, Adam, and
             the full-batch reconstruction loop (Sec. 4.3), plus the phi = 0
             render and the fat/water split (Sec. 4.3, Sec. 6)
+  projection  the paper's own forward model (Sec. 4.2): interpolated
+            projection at the blade's tilt, centred DFT and blade mask; its
+            adjoint; the image- plus k-space loss with TV (x-y, spectral,
+            time) and L1, and Adam over the blades in turn (Sec. 4.3)
 
 Every function is pinned by a ``-m "not gpu"`` test against something other
 than itself (library special cases, closed forms, invariants, brute force,
@@ -27,9 +31,10 @@ from .geometry import Geometry, make_geometry, sample_coords, phase_table
 from .ndft import forward, adjoint, forward_at, adjoint_at
 from .recon import (ReconParams, data_loss, tv_xy, tv_t, loss_and_grad,
                     adam_step, reconstruct, render)
+from . import projection
 
 __all__ = [
     "Geometry", "make_geometry", "sample_coords", "phase_table", "forward", "adjoint",
     "forward_at", "adjoint_at", "ReconParams", "data_loss", "tv_xy", "tv_t",
-    "loss_and_grad", "adam_step", "reconstruct", "render",
+    "loss_and_grad", "adam_step", "reconstruct", "render", "projection",
 ]

@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-projection", action="store_true",
+                    help="skip the projection-model (the paper's own forward model) measurement")
     ap.add_argument("--bin-chunk", type=int, default=0, help="bins per grid pass (0: the plan's default)")
     ap.add_argument("--row-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="row kernel: 0 the plan's choice, 1 per-row CTAs, 2 warp-specialised")
@@ -501,11 +503,54 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline_obj()
         if world == 1 and not args.no_serving and args.serve_requests > 0 and args.workload == WORKLOAD:
             line["serving"] = run_serving(args.serve_requests, args.serve_iters, 7, local)
+        if world == 1 and not args.no_projection and args.workload == WORKLOAD:
+            line["projection_model"] = run_projection_model(plan, w, prob, dev, peak, K)
         print(json.dumps(line), flush=True)
     plan.destroy()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_projection_model(plan, w, prob, dev, peak, K):
+    """The paper's own forward model (interpolated projection, Cartesian DFT
+    and blade mask, image- plus k-space loss, one blade per iteration) on the
+    same plan: Cartesian blade data of the same phantom, one
+    prop_proj_reconstruct call of K iterations timed with CUDA events.
+    Algorithmic bytes per iteration: the projected frame of V (|V| / T), V, m
+    and v read and written by the update (6 |V|), and ten passes over an
+    N x N complex image (projection, four transform passes, the gradient)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2311_13177_gb300 import ProjParams
+    rng = np.random.default_rng(w.seed + 1)
+    yc = synth.simulate_cartesian_blades(prob["ellipses"], w.N, prob["theta"], w.fat_shift)
+    yc = synth.add_noise(yc, w.rel_sigma, rng).astype(np.complex64)
+    ycart = torch.from_numpy(yc).to(dev)
+    q = dict(lr=w.lr, w_kspace=0.1, w_image=1.0, tv_xy=1e-3, tv_f=1e-3, l1=1e-4, tv_eps=w.tv_eps)
+    V = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)
+    plan.proj_reconstruct(ycart, ProjParams(iters=5, **q), V=V, trace=False)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    V.zero_()
+    e0.record(s)
+    plan.proj_reconstruct(ycart, ProjParams(iters=K, **q), V=V, trace=False)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, tr = plan.proj_reconstruct(ycart, ProjParams(iters=2 * w.B, **q), V=torch.zeros_like(V), trace=True)
+    vol = 8.0 * float(np.prod(plan.vol_shape))
+    b_iter = vol / w.T + 6.0 * vol + 10.0 * 8.0 * w.N * w.N
+    rate = K / (ms / 1000.0)
+    return {"value": rate, "unit": "iters/s", "ms_per_iter": ms / K, "iters": K,
+            "config": f"{w.N}x{w.N}, {w.Nf} bins, {w.B} blades (Cartesian masks of {w.L} x {w.R}), one blade "
+                      f"per iteration; w_k 0.1, w_i 1, TV_xy 1e-3, TV_f 1e-3, L1 1e-4",
+            "roofline": {"bound": "hbm", "algo_bytes_per_iter": b_iter, "achieved_gbs": b_iter * rate / 1e9,
+                         "peak": peak, "frac": b_iter * rate / 1e9 / peak,
+                         "roofline_iters_per_s": peak * 1e9 / b_iter},
+            "loss_first_pass": float(np.sum(tr[:w.B])), "loss_second_pass": float(np.sum(tr[w.B:]))}
 
 
 def run_diff_study(args):

@@ -295,6 +295,49 @@ PROP_API prop_status prop_fp32_fma_peak(int device, double* tflops);
  * device), PROP_ERR_CUDA. */
 PROP_API prop_status prop_check_bounded_wait(int device, long long limit_cycles, int* expired, double* ms);
 
+/* ---- The paper's own forward model (Sec. 4.2-4.3) ----------------------
+ *
+ * Projection: blade b's image is I_b(p) = sum_f bilinear(V_t(b)(., f), p - Delta_f d_b)
+ * (one sample per spectral slice along the ray tilted towards the readout
+ * direction, Delta_f = h_f tan(phi); zero outside the image).  Blur: the
+ * centred unitary DFT Z = U I_b (Z(k) = (1/N) sum_x I(x) e^{-2 pi i k.x},
+ * k = (u - N/2)/N), masked by the blade's support M_b: the Cartesian cells
+ * whose rotated coordinates rho = N k.d_b, pi = N k.d_b^perp satisfy
+ * -R/2 - 1/2 <= rho < R/2 - 1/2 and -L/2 - 1/2 <= pi < L/2 - 1/2.  Uses the
+ * plan's N (>= 16), Nf, Delta_f, theta_b, L, R, T and blade frames; tables
+ * and a few N x N work images are allocated on first use.
+ *
+ * Cartesian k-space arrays are [N][N] complex64 indexed [u2][u1]; images
+ * [N][N] indexed [i2][i1] (x = i - N/2); volumes as above. */
+typedef struct prop_proj_params {
+  int iters;                     /* K >= 0 iterations; iteration k (1-based) uses blade (k - 1) mod B */
+  float lr, beta1, beta2, eps;   /* Adam */
+  float w_kspace, w_image;       /* weights of the k-space and image-space data terms (Sec. 4.3) */
+  float tv_xy, tv_f, tv_t;       /* smoothed TV along x1/x2, along the spectral axis, along time */
+  float l1;                      /* smoothed L1 sparsity weight, l1 * sum sqrt(|V|^2 + tv_eps^2) */
+  float tv_eps;                  /* smoothing epsilon (> 0) */
+} prop_proj_params;
+
+/* z = M_b U P_b V_t(b): [N][N] complex64 on the device, zero outside the
+ * mask.  Errors: PROP_ERR_INVALID_ARG (null, blade out of range, N < 16),
+ * PROP_ERR_OOM, PROP_ERR_CUDA.  Does not synchronise. */
+PROP_API prop_status prop_proj_forward(prop_plan plan, int blade, const void* V_dev, void* z_dev, void* stream);
+/* V = P_b^H U^H M_b z: frame t(b) of the volume gets the transposed
+ * projection, the other frames zero.  Does not synchronise. */
+PROP_API prop_status prop_proj_adjoint(prop_plan plan, int blade, const void* z_dev, void* V_dev, void* stream);
+/* Adam over the blades in turn (Sec. 4.3) on
+ *   w_kspace sum_{M_b} |Z - ycart_b|^2 + w_image sum |U^H M_b Z - img_b|^2
+ *   + tv_xy TV_xy + tv_f TV_f + tv_t TV_t + l1 L1,   Z = U P_b V_t(b),
+ * each TV term sum sqrt(|d|^2 + tv_eps^2) over forward differences (no wrap).
+ * ycart_dev: [B][N][N] Cartesian k-space data (cells outside each mask are
+ * not read); img_dev: [B][N][N] blade images, or NULL for U^H M_b ycart_b.
+ * V_dev: the start in, the result out.  loss_trace_host (may be NULL):
+ * [iters] loss of each iteration's blade before its update.  Synchronises
+ * only when a trace is requested. */
+PROP_API prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev, const void* img_dev,
+                                           const prop_proj_params* params, void* V_dev, double* loss_trace_host,
+                                           void* stream);
+
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 PROP_API const char* prop_last_error(void);
 

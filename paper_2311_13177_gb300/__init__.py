@@ -5,11 +5,11 @@ The compute lives in ``lib/libprop.so`` (built from ``csrc/`` by
 arguments.  Importing the package does not load the library; the first call
 does, and it raises if the library is missing.
 """
-from .binding import (Plan, ReconParams, prop_plan_create, prop_plan_destroy, prop_plan_workspace_bytes,
+from .binding import (Plan, ReconParams, ProjParams, prop_plan_create, prop_plan_destroy, prop_plan_workspace_bytes,
                       prop_forward, prop_adjoint, prop_reconstruct, prop_reconstruct_host, prop_loss_grad,
                       prop_render)
 from .autograd import PropOp, prop_apply
 
-__all__ = ["Plan", "ReconParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
+__all__ = ["Plan", "ReconParams", "ProjParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
            "prop_forward", "prop_adjoint", "prop_reconstruct", "prop_reconstruct_host", "prop_loss_grad",
            "prop_render", "PropOp", "prop_apply"]

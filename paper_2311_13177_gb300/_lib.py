@@ -36,6 +36,12 @@ class ReconParamsC(ctypes.Structure):
                 ("eps", c_float), ("tv_xy", c_float), ("tv_t", c_float), ("tv_eps", c_float)]
 
 
+class ProjParamsC(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("lr", c_float), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
+                ("w_kspace", c_float), ("w_image", c_float), ("tv_xy", c_float), ("tv_f", c_float),
+                ("tv_t", c_float), ("l1", c_float), ("tv_eps", c_float)]
+
+
 # name -> (restype, argtypes); every symbol include/prop.h declares.
 SIGNATURES = {
     "prop_plan_create": (c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(c_void_p)]),
@@ -67,6 +73,10 @@ SIGNATURES = {
     "prop_profile_enable": (c_int, [c_void_p, c_int]),
     "prop_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "prop_fp32_fma_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "prop_proj_forward": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "prop_proj_adjoint": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "prop_proj_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(ProjParamsC), c_void_p,
+                                      ctypes.POINTER(c_double), c_void_p]),
     "prop_check_bounded_wait": (c_int, [c_int, ctypes.c_longlong, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "prop_last_error": (ctypes.c_char_p, []),
 }

@@ -5,7 +5,8 @@ current CUDA stream, numpy arrays supply host buffers; every step of the
 operator, adjoint, loss and optimiser runs in libprop's kernels.
 
 Layouts (complex64): V [T, N, N, Nf] (index [t, i2, i1, f], x = i - N/2),
-y [B, L, R], image [T, N, N].
+y [B, L, R], image [T, N, N]; projection model: Cartesian k-space [N, N]
+(index [u2, u1], k = (u - N/2)/N), per-blade data [B, N, N].
 """
 from __future__ import annotations
 
@@ -15,9 +16,9 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._lib import PlanDesc, ReconParamsC, check, lib
+from ._lib import PlanDesc, ProjParamsC, ReconParamsC, check, lib
 
-__all__ = ["Plan", "ReconParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
+__all__ = ["Plan", "ReconParams", "ProjParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
            "prop_forward", "prop_adjoint", "prop_reconstruct", "prop_reconstruct_host",
            "prop_loss_grad", "prop_render"]
 
@@ -36,6 +37,28 @@ class ReconParams:
     def c(self) -> ReconParamsC:
         return ReconParamsC(int(self.iters), float(self.lr), float(self.beta1), float(self.beta2),
                             float(self.eps), float(self.tv_xy), float(self.tv_t), float(self.tv_eps))
+
+
+@dataclass
+class ProjParams:
+    """Settings of prop_proj_reconstruct (the paper's own forward model)."""
+    iters: int = 20
+    lr: float = 1e-2
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    w_kspace: float = 0.1
+    w_image: float = 1.0
+    tv_xy: float = 1e-3
+    tv_f: float = 0.0
+    tv_t: float = 0.0
+    l1: float = 0.0
+    tv_eps: float = 1e-3
+
+    def c(self) -> ProjParamsC:
+        return ProjParamsC(int(self.iters), float(self.lr), float(self.beta1), float(self.beta2), float(self.eps),
+                           float(self.w_kspace), float(self.w_image), float(self.tv_xy), float(self.tv_f),
+                           float(self.tv_t), float(self.l1), float(self.tv_eps))
 
 
 def _stream(stream=None) -> ctypes.c_void_p:
@@ -193,6 +216,42 @@ class Plan:
               "prop_render")
         return out
 
+
+    @property
+    def kspace_shape(self):
+        return (self.N, self.N)
+
+    def proj_forward(self, blade: int, V: torch.Tensor, z: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """Masked Cartesian k-space of one blade under the projection model."""
+        if z is None:
+            z = torch.empty(self.kspace_shape, dtype=torch.complex64, device=V.device)
+        check(lib().prop_proj_forward(self.handle, int(blade), _dev_ptr(V, self.vol_shape, "V"),
+                                      _dev_ptr(z, self.kspace_shape, "z"), _stream(stream)), "prop_proj_forward")
+        return z
+
+    def proj_adjoint(self, blade: int, z: torch.Tensor, V: torch.Tensor = None, stream=None) -> torch.Tensor:
+        if V is None:
+            V = torch.empty(self.vol_shape, dtype=torch.complex64, device=z.device)
+        check(lib().prop_proj_adjoint(self.handle, int(blade), _dev_ptr(z, self.kspace_shape, "z"),
+                                      _dev_ptr(V, self.vol_shape, "V"), _stream(stream)), "prop_proj_adjoint")
+        return V
+
+    def proj_reconstruct(self, ycart: torch.Tensor, params: "ProjParams", img: torch.Tensor = None,
+                         V: torch.Tensor = None, trace=True, stream=None):
+        """Adam over the blades in turn under the projection model, in place on V (zeros if None).
+
+        Returns (V, loss_trace numpy array or None)."""
+        if V is None:
+            V = torch.zeros(self.vol_shape, dtype=torch.complex64, device=ycart.device)
+        shp = (self.B, self.N, self.N)
+        ip = _dev_ptr(img, shp, "img") if img is not None else None
+        tr = np.zeros(max(params.iters, 1), dtype=np.float64) if trace else None
+        tr_ptr = tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None
+        pc = params.c()
+        check(lib().prop_proj_reconstruct(self.handle, _dev_ptr(ycart, shp, "ycart"), ip, ctypes.byref(pc),
+                                          _dev_ptr(V, self.vol_shape, "V"), tr_ptr, _stream(stream)),
+              "prop_proj_reconstruct")
+        return V, (tr[:params.iters] if trace else None)
 
     def profile_enable(self, on: bool = True) -> None:
         check(lib().prop_profile_enable(self.handle, 1 if on else 0), "prop_profile_enable")

@@ -1095,6 +1095,163 @@ cudaError_t dispatch_fused(int n, const FusedArgs& a, bool fwd_tail, dim3 grid, 
   }
 }
 
+// --- Centred unitary 2-D DFT of one N x N image (projection model) ----------
+//
+// Four passes of NFFT = N point transforms, 16 lines per CTA: forward rows,
+// forward columns (scale 1/N; optionally masked, or fused with the blade's
+// data term), inverse columns (input optionally masked), inverse rows (scale
+// 1/N).  The centring (image index i = x + N/2, k index u = N k + N/2) is
+// the index map position -> (position + N/2) mod N on every input and
+// output, which is where an unshifted DFT's position 0 holds x = 0 / k = 0.
+struct CartArgs {
+  const float2* src;
+  float2* dst;
+  const float2* twiddle;  // [N] exp(-2 pi i m / N)
+  const uint8_t* mask;    // [N][N] blade support, or null
+  const float2* y;        // data term: [N][N] k-space data of the blade
+  const float2* yimg;     // data term: [N][N] DFT of the blade's image, or null (= y)
+  float wk, wi;
+  double* partials;
+  unsigned int* counter;
+  const double* loss_const;
+  double* loss_out;
+  int N;
+  float scale;
+};
+
+__device__ __forceinline__ int cshift(int p, int N) {
+  const int q = p + (N >> 1);
+  return q >= N ? q - N : q;
+}
+// Lines are the rows r0 + col (elements contiguous).
+struct InCartRows {
+  const float2* src;
+  int N;
+  size_t r0;
+  __device__ float2 operator()(int pos, int col) const { return src[(r0 + col) * N + cshift(pos, N)]; }
+};
+struct OutCartRows {
+  float2* dst;
+  int N;
+  size_t r0;
+  float scale;
+  __device__ void operator()(int q, int col, float2 v) const { dst[(r0 + col) * N + cshift(q, N)] = cscale(v, scale); }
+};
+// Lines are the columns c0 + col (elements N apart).
+struct InCartCols {
+  const float2* src;
+  const uint8_t* mask;
+  int N, c0;
+  __device__ float2 operator()(int pos, int col) const {
+    const size_t i = (size_t)cshift(pos, N) * N + c0 + col;
+    if (mask && !mask[i]) return make_float2(0.f, 0.f);
+    return src[i];
+  }
+};
+struct OutCartCols {
+  float2* dst;
+  const uint8_t* mask;
+  int N, c0;
+  float scale;
+  __device__ void operator()(int q, int col, float2 v) const {
+    const size_t i = (size_t)cshift(q, N) * N + c0 + col;
+    float2 z = cscale(v, scale);
+    if (mask && !mask[i]) z = make_float2(0.f, 0.f);
+    dst[i] = z;
+  }
+};
+// Forward column output fused with the blade's data term: on the mask,
+// r_k = Z - y, r_i = Z - yimg (the image term through the unitary DFT),
+// loss += wk |r_k|^2 + wi |r_i|^2 and dst = 2 (wk r_k + wi r_i); 0 elsewhere.
+struct OutCartLoss {
+  float2* dst;
+  const uint8_t* mask;
+  const float2* y;
+  const float2* yimg;
+  float wk, wi;
+  int N, c0;
+  float scale;
+  float* acc;
+  __device__ void operator()(int q, int col, float2 v) const {
+    const size_t i = (size_t)cshift(q, N) * N + c0 + col;
+    float2 g = make_float2(0.f, 0.f);
+    if (mask[i]) {
+      const float2 z = cscale(v, scale);
+      const float2 yy = y[i];
+      const float2 yi = yimg ? yimg[i] : yy;
+      const float2 rk = make_float2(z.x - yy.x, z.y - yy.y);
+      const float2 ri = make_float2(z.x - yi.x, z.y - yi.y);
+      *acc += wk * fmaf(rk.x, rk.x, rk.y * rk.y) + wi * fmaf(ri.x, ri.x, ri.y * ri.y);
+      g = make_float2(2.f * fmaf(wk, rk.x, wi * ri.x), 2.f * fmaf(wk, rk.y, wi * ri.y));
+    }
+    dst[i] = g;
+  }
+};
+
+template <int NFFT, int PASS>
+__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS) cart_fft_kernel(CartArgs a) {
+  constexpr int EV = kValsPlain<NFFT>;
+  extern __shared__ float2 smem[];
+  float2* X = smem;
+  float2* tw = smem + NFFT * kFftCols;
+  build_twiddles<NFFT>(tw, a.twiddle);
+  grid_dep_wait();
+  grid_dep_release();
+  __syncthreads();
+  const int col = threadIdx.x % kFftCols;
+  const int tl = threadIdx.x / kFftCols;
+  const int l0 = blockIdx.x * kFftCols;
+  if constexpr (PASS == kCartRowsFwd) {
+    InCartRows in{a.src, NFFT, (size_t)l0};
+    OutCartRows out{a.dst, NFFT, (size_t)l0, a.scale};
+    fft_pass<NFFT, EV, -1, 0, 1, false, false>(X, tw, col, tl, in, out);
+  } else if constexpr (PASS == kCartColsFwd) {
+    InCartCols in{a.src, nullptr, NFFT, l0};
+    if (a.y) {
+      float acc = 0.f;
+      OutCartLoss out{a.dst, a.mask, a.y, a.yimg, a.wk, a.wi, NFFT, l0, a.scale, &acc};
+      fft_pass<NFFT, EV, -1, 0, 1, false, false>(X, tw, col, tl, in, out);
+      finish_loss(acc, a.partials, a.counter, a.loss_const, a.loss_out);
+    } else {
+      OutCartCols out{a.dst, a.mask, NFFT, l0, a.scale};
+      fft_pass<NFFT, EV, -1, 0, 1, false, false>(X, tw, col, tl, in, out);
+    }
+  } else if constexpr (PASS == kCartColsInv) {
+    InCartCols in{a.src, a.mask, NFFT, l0};
+    OutCartCols out{a.dst, nullptr, NFFT, l0, a.scale};
+    fft_pass<NFFT, EV, +1, 0, 1, false, false>(X, tw, col, tl, in, out);
+  } else {
+    InCartRows in{a.src, NFFT, (size_t)l0};
+    OutCartRows out{a.dst, NFFT, (size_t)l0, a.scale};
+    fft_pass<NFFT, EV, +1, 0, 1, false, false>(X, tw, col, tl, in, out);
+  }
+}
+
+template <int NFFT>
+cudaError_t launch_cart(int pass, const CartArgs& a, cudaStream_t s) {
+  const dim3 grid(NFFT / kFftCols), block(Shape<NFFT, kValsPlain<NFFT>>::THREADS);
+  const size_t smem = Shape<NFFT, kValsPlain<NFFT>>::SMEM;
+  switch (pass) {
+    case kCartRowsFwd: return launch_dep(cart_fft_kernel<NFFT, kCartRowsFwd>, grid, block, smem, s, a);
+    case kCartColsFwd: return launch_dep(cart_fft_kernel<NFFT, kCartColsFwd>, grid, block, smem, s, a);
+    case kCartColsInv: return launch_dep(cart_fft_kernel<NFFT, kCartColsInv>, grid, block, smem, s, a);
+    default: return launch_dep(cart_fft_kernel<NFFT, kCartRowsInv>, grid, block, smem, s, a);
+  }
+}
+
+template <int NFFT>
+cudaError_t configure_cart() {
+  const int smem = (int)Shape<NFFT, kValsPlain<NFFT>>::SMEM;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(cart_fft_kernel<NFFT, kCartRowsFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(cart_fft_kernel<NFFT, kCartColsFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(cart_fft_kernel<NFFT, kCartColsInv>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  return cudaFuncSetAttribute(cart_fft_kernel<NFFT, kCartRowsInv>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t dispatch_fused_ws(int n, const CUtensorMap& tm, const FusedArgs& a, bool fwd_tail, int ctas,
                               cudaStream_t s) {
   switch (n) {
@@ -1268,6 +1425,46 @@ cudaError_t fused_rows_update(const Plan& p, const float2* Vin, float2* m, float
   dim3 grid((p.Nf + kFftCols - 1) / kFftCols, p.T * p.N);
   if ((long)grid.x * grid.y > red->capacity) return cudaErrorInvalidValue;
   return dispatch_fused(p.n, a, fwd_tail, grid, s);
+}
+
+
+cudaError_t cart_fft_configure(int N) {
+  switch (N) {
+#define CASE(v) \
+  case v: return configure_cart<v>();
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t cart_fft_pass(int N, int pass, const float2* src, float2* dst, const float2* twiddleN,
+                          const uint8_t* mask, const CartLoss* loss, float scale, cudaStream_t s) {
+  CartArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.twiddle = twiddleN;
+  a.mask = mask;
+  a.N = N;
+  a.scale = scale;
+  if (loss) {
+    if (pass != kCartColsFwd || !loss->red || !mask || loss->red->capacity < N / kFftCols) return cudaErrorInvalidValue;
+    a.y = loss->y;
+    a.yimg = loss->yimg;
+    a.wk = loss->wk;
+    a.wi = loss->wi;
+    a.partials = loss->red->partials;
+    a.counter = loss->red->counter;
+    a.loss_const = loss->loss_const;
+    a.loss_out = loss->loss_out;
+  }
+  switch (N) {
+#define CASE(v) \
+  case v: return launch_cart<v>(pass, a, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace prop

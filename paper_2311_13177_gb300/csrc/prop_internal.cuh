@@ -157,6 +157,20 @@ struct Plan {
   float2* rows = nullptr;        // [T][N][n][chunk] row-pass intermediate
   float2* contrib = nullptr;     // [M + 1][cs] conj(P[j][f]) r_m, input of the spread; row M stays zero
 
+  // projection model, the paper's own forward model (allocated on first use)
+  bool proj_ready = false;
+  int4* proj_shift = nullptr;      // [B][Nf] (o1, o2, w1 bits, w2 bits): along axis a pixel i reads
+                                   // taps i + o_a (weight 1 - w_a) and i + o_a + 1 (weight w_a)
+  uint8_t* proj_mask = nullptr;    // [B][N][N] blade support on the Cartesian k grid
+  float2* proj_twiddle = nullptr;  // [N] exp(-2 pi i m / N)
+  float2* proj_img = nullptr;      // [N][N] projected image
+  float2* proj_k = nullptr;        // [N][N] transform work
+  float2* proj_kg = nullptr;       // [N][N] k-space gradient of the data term
+  float2* proj_g = nullptr;        // [N][N] its inverse DFT (image-space gradient)
+  float2* proj_yimg = nullptr;     // [B][N][N] DFT of the given blade images
+  double* proj_const = nullptr;    // [B] image term outside each mask
+  Reducer red_proj_k, red_proj_u;
+
   // reconstruction state (allocated on first use)
   bool recon_ready = false;
   float2* resid = nullptr;       // [M]
@@ -222,6 +236,27 @@ cudaError_t fft_forward_cols(const Plan& p, cudaStream_t s);
 cudaError_t fft_adjoint_cols(const Plan& p, cudaStream_t s);
 cudaError_t fft_adjoint_rows(const Plan& p, float2* out, int f0, float scale, cudaStream_t s);
 cudaError_t fft_configure(int n);
+// proj.cu: tables and workspace of the projection model; `images`: also the
+// per-blade image spectra.
+prop_status plan_ensure_proj(Plan& p, bool images);
+// Centred unitary 2-D DFT of one N x N image, [i2][i1] <-> [u2][u1] (projection
+// model): one pass of N-point transforms over the rows or the columns.
+enum CartPass { kCartRowsFwd = 0, kCartColsFwd = 1, kCartColsInv = 2, kCartRowsInv = 3 };
+struct CartLoss {              // blade data term fused into the forward column pass
+  const float2* y;             // [N][N] k-space data of the blade
+  const float2* yimg;          // [N][N] DFT of the blade's image, or null (image term against y)
+  float wk, wi;                // k-space and image-space weights
+  const Reducer* red;          // >= N/16 partials
+  const double* loss_const;    // added to the data loss (image term outside the mask), or null
+  double* loss_out;
+};
+// kCartColsFwd writes Z * scale masked by `mask` (when given), or with `loss`
+// the data-term gradient 2 M (wk (Z - y) + wi (Z - yimg)) and the loss;
+// kCartColsInv masks its input by `mask` (when given).  Rows passes and the
+// inverse column pass multiply by `scale`.
+cudaError_t cart_fft_pass(int N, int pass, const float2* src, float2* dst, const float2* twiddleN,
+                          const uint8_t* mask, const CartLoss* loss, float scale, cudaStream_t s);
+cudaError_t cart_fft_configure(int N);
 // Builds the column passes' tensor maps (after the workspaces exist) and
 // decides whether the staged column kernels fit this plan; never fails the
 // plan (the unstaged kernels remain).

@@ -109,7 +109,17 @@ __device__ __forceinline__ float2 adam_voxel(float2 x, float2 g, float2& mm, flo
 }
 
 // Block sum of one double per thread; valid in thread 0 (all threads call).
+// sh holds 32 doubles.
 __device__ __forceinline__ double block_sum_tv(double v, double* sh) {
+  if (blockDim.x < 32) {  // narrower than a warp (length-16 transforms): no full-warp shuffles
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+      for (int i = 0; i < (int)blockDim.x; ++i) t += sh[i];
+    __syncthreads();
+    return t;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

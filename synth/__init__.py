@@ -14,11 +14,11 @@ Sec. 3 and Sec. 5) stand in for them.
 """
 
 from .phantom import (Ellipse, random_ellipses, ellipse_ft, simulate_blades,
-                      add_noise, rasterize, blade_kspace)
+                      simulate_cartesian_blades, add_noise, rasterize, blade_kspace)
 from .workloads import WORKLOADS, Workload, make_problem, make_serve_requests
 
 __all__ = [
-    "Ellipse", "random_ellipses", "ellipse_ft", "simulate_blades", "add_noise",
+    "Ellipse", "random_ellipses", "ellipse_ft", "simulate_blades", "simulate_cartesian_blades", "add_noise",
     "rasterize", "blade_kspace", "WORKLOADS", "Workload", "make_problem",
     "make_serve_requests",
 ]

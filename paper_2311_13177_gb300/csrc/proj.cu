@@ -34,43 +34,64 @@ constexpr int kProjThreads = 256;
 // Projected image of blade b, frame t: img[i2][i1] = sum_f bilinear(V_t[., ., f],
 // (i1, i2) - s_f).  sh[f] = (o1, o2, w1 bits, w2 bits): along axis a the
 // pixel reads taps i + o_a (weight 1 - w_a) and i + o_a + 1 (weight w_a).
+// A warp takes kProjPix adjacent pixels of one row, its lanes the bins: the
+// pixels share all but one of their x1 taps, so each bin loads kProjPix + 1
+// values per tap row.
+constexpr int kProjPix = 4;
 __global__ void __launch_bounds__(kProjThreads) proj_image_kernel(const float2* __restrict__ V,
                                                                   const int4* __restrict__ sh, int N, int Nf, int t,
                                                                   float2* __restrict__ img) {
   grid_dep_wait();
   grid_dep_release();
   const int lane = threadIdx.x & 31;
-  const long pix = (long)blockIdx.x * (kProjThreads / 32) + (threadIdx.x >> 5);
-  if (pix >= (long)N * N) return;  // whole warps leave together
-  const int i2 = (int)(pix / N), i1 = (int)(pix - (long)i2 * N);
+  const long pix0 = ((long)blockIdx.x * (kProjThreads / 32) + (threadIdx.x >> 5)) * kProjPix;
+  if (pix0 >= (long)N * N) return;  // whole warps leave together
+  const int i2 = (int)(pix0 / N), i10 = (int)(pix0 - (long)i2 * N);  // N % kProjPix == 0: one row
   const float2* Vt = V + (size_t)t * N * N * Nf;
-  float ax = 0.f, ay = 0.f;
+  float ax[kProjPix], ay[kProjPix];
+#pragma unroll
+  for (int q = 0; q < kProjPix; ++q) ax[q] = ay[q] = 0.f;
   for (int f = lane; f < Nf; f += 32) {
     const int4 o = __ldg(&sh[f]);
     const float w1 = __int_as_float(o.z), w2 = __int_as_float(o.w);
-    const int j1 = i1 + o.x, j2 = i2 + o.y;
+    const int j1 = i10 + o.x, j2 = i2 + o.y;
 #pragma unroll
     for (int d2 = 0; d2 < 2; ++d2) {
       const int r = j2 + d2;
       if (r < 0 || r >= N) continue;
       const float c2 = d2 ? w2 : 1.f - w2;
+      float2 v[kProjPix + 1];
 #pragma unroll
-      for (int d1 = 0; d1 < 2; ++d1) {
-        const int c = j1 + d1;
-        if (c < 0 || c >= N) continue;
-        const float w = c2 * (d1 ? w1 : 1.f - w1);
-        const float2 v = __ldg(&Vt[((size_t)r * N + c) * Nf + f]);
-        ax = fmaf(w, v.x, ax);
-        ay = fmaf(w, v.y, ay);
+      for (int k = 0; k <= kProjPix; ++k) {
+        const int c = j1 + k;
+        v[k] = (c >= 0 && c < N) ? __ldg(&Vt[((size_t)r * N + c) * Nf + f]) : make_float2(0.f, 0.f);
+      }
+      const float wl = c2 * (1.f - w1), wh = c2 * w1;
+#pragma unroll
+      for (int q = 0; q < kProjPix; ++q) {
+        ax[q] = fmaf(wh, v[q + 1].x, fmaf(wl, v[q].x, ax[q]));
+        ay[q] = fmaf(wh, v[q + 1].y, fmaf(wl, v[q].y, ay[q]));
       }
     }
   }
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    ax += __shfl_xor_sync(0xffffffffu, ax, s);
-    ay += __shfl_xor_sync(0xffffffffu, ay, s);
+  for (int q = 0; q < kProjPix; ++q) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      ax[q] += __shfl_xor_sync(0xffffffffu, ax[q], s);
+      ay[q] += __shfl_xor_sync(0xffffffffu, ay[q], s);
+    }
   }
-  if (lane == 0) img[pix] = make_float2(ax, ay);
+  if (lane < kProjPix) {
+    float bx = ax[0], by = ay[0];
+#pragma unroll
+    for (int q = 1; q < kProjPix; ++q)
+      if (lane == q) {
+        bx = ax[q];
+        by = ay[q];
+      }
+    img[pix0 + lane] = make_float2(bx, by);
+  }
 }
 
 // Transposed projection at voxel (i2, i1, f): pixel p reads voxel p + o
@@ -134,33 +155,63 @@ struct ProjUpdArgs {
 // Fused update: data gradient by the transposed projection, TV along x1, x2
 // and t (the same arithmetic as the non-uniform model's update), TV along
 // the spectral axis, L1, Adam, and the FP64 loss of the iterate it reads.
+// Grid: (blocks per image row, T N rows); 32-bit index math within a row.
+// Every neighbour load is unconditional (a missing neighbour reads the voxel
+// itself and is not used), so the loads of several voxels are in flight
+// together; TT: the volume has time neighbours.
+template <bool TT>
 __global__ void __launch_bounds__(kProjThreads) proj_update_kernel(ProjUpdArgs a) {
   grid_dep_wait();
   grid_dep_release();
-  const size_t total = (size_t)a.T * a.N * a.N * a.Nf;
+  const int row = blockIdx.y;  // t N + i2
+  const int i2 = row % a.N, t = row / a.N;
+  const int rl = a.N * a.Nf;
+  const size_t base = (size_t)row * rl;
+  const size_t sx = (size_t)a.Nf, sy = (size_t)rl, st = (size_t)a.N * rl;
   const float eps2 = a.ad.tv_eps * a.ad.tv_eps;
+  const bool xy = a.ad.tv_xy != 0.f;
+  const bool h2p = xy && i2 + 1 < a.N, h2m = xy && i2 > 0;
+  const bool htp = TT && t + 1 < a.T, htm = TT && t > 0;
+  const bool data = t == a.tb;
   const float2* __restrict__ Vin = a.Vin;
   float local = 0.f;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int f = (int)(idx % a.Nf);
-    size_t r = idx / a.Nf;
-    const int i1 = (int)(r % a.N);
-    r /= a.N;
-    const int i2 = (int)(r % a.N);
-    const int t = (int)(r / a.N);
+#pragma unroll 2
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rl; e += gridDim.x * blockDim.x) {
+    const int i1 = e / a.Nf;
+    const int f = e - i1 * a.Nf;
+    const size_t idx = base + e;
     const float2 x = Vin[idx];
-    const float2 gd = t == a.tb ? proj_gather(a.gimg, __ldg(&a.sh[f]), a.N, i1, i2) : make_float2(0.f, 0.f);
+    TvNbrs nb;
+    nb.h1p = xy && i1 + 1 < a.N;
+    nb.h1m = xy && i1 > 0;
+    nb.h2p = h2p;
+    nb.h2m = h2m;
+    nb.htp = htp;
+    nb.htm = htm;
+    nb.x1p = Vin[nb.h1p ? idx + sx : idx];
+    nb.x1m = Vin[nb.h1m ? idx - sx : idx];
+    nb.x2p = Vin[h2p ? idx + sy : idx];
+    nb.x2m = Vin[h2m ? idx - sy : idx];
+    if constexpr (TT) {
+      nb.tp = Vin[htp ? idx + st : idx];
+      nb.tm = Vin[htm ? idx - st : idx];
+    } else {
+      nb.tp = nb.tm = x;
+    }
+    const bool hfp = a.tv_f != 0.f && f + 1 < a.Nf, hfm = a.tv_f != 0.f && f > 0;
+    const float2 xfp = Vin[hfp ? idx + 1 : idx];
+    const float2 xfm = Vin[hfm ? idx - 1 : idx];
+    float2 mm = a.m[idx], vv = a.v[idx];
+    const float2 gd = data ? proj_gather(a.gimg, __ldg(&a.sh[f]), a.N, i1, i2) : make_float2(0.f, 0.f);
     float2 gxy, gt;
-    float tv = voxel_tv(Vin, idx, x, i1, i2, t, a.N, a.Nf, a.T, a.ad.tv_xy, a.ad.tv_t, eps2, &gxy, &gt);
+    float tv = voxel_tv_nb(x, nb, a.ad.tv_xy, TT ? a.ad.tv_t : 0.f, eps2, &gxy, &gt);
     float2 gf = make_float2(0.f, 0.f);
     float mag;
-    if (a.tv_f != 0.f) {
-      if (f + 1 < a.Nf) {
-        gf = csub_rn(gf, tv_term(csub_rn(Vin[idx + 1], x), eps2, &mag));
-        tv = fmaf(a.tv_f, mag, tv);
-      }
-      if (f > 0) gf = cadd_rn(gf, tv_term(csub_rn(x, Vin[idx - 1]), eps2, &mag));
+    if (hfp) {
+      gf = csub_rn(gf, tv_term(csub_rn(xfp, x), eps2, &mag));
+      tv = fmaf(a.tv_f, mag, tv);
     }
+    if (hfm) gf = cadd_rn(gf, tv_term(csub_rn(x, xfm), eps2, &mag));
     float2 gl = make_float2(0.f, 0.f);
     if (a.l1 != 0.f) {
       gl = tv_term(x, eps2, &mag);  // x / sqrt(|x|^2 + eps^2) and the smoothed modulus
@@ -170,7 +221,6 @@ __global__ void __launch_bounds__(kProjThreads) proj_update_kernel(ProjUpdArgs a
     g.x = fmaf(a.l1, gl.x, fmaf(a.tv_f, gf.x, g.x));
     g.y = fmaf(a.l1, gl.y, fmaf(a.tv_f, gf.y, g.y));
     local = __fadd_rn(local, tv);
-    float2 mm = a.m[idx], vv = a.v[idx];
     const float2 nx = adam_voxel(x, g, mm, vv, a.ad);
     a.m[idx] = mm;
     a.v[idx] = vv;
@@ -196,10 +246,10 @@ __global__ void __launch_bounds__(kProjThreads) proj_const_kernel(const float2* 
   if (threadIdx.x == 0) c[blockIdx.x] = (double)wi * s;
 }
 
-int update_blocks(const Plan& p) {
-  const size_t total = (size_t)p.T * p.N * p.N * p.Nf;
-  const size_t want = (total + kProjThreads - 1) / kProjThreads;
-  return (int)std::max<size_t>(1, std::min<size_t>(want, (size_t)p.red_proj_u.capacity));
+// Blocks per image row of the update: about 8 voxels a thread, at most 4.
+int update_row_blocks(const Plan& p) {
+  const int rl = p.N * p.Nf;
+  return std::max(1, std::min(4, rl / (8 * kProjThreads)));
 }
 
 prop_status proj_alloc(Plan& p, void** ptr, size_t bytes, const char* what) {
@@ -262,7 +312,7 @@ prop_status plan_ensure_proj(Plan& p, bool images) {
       const double a = -2.0 * M_PI * m / N;
       tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
-    const int red_u = 8 * p.num_sms;
+    const int red_u = update_row_blocks(p) * p.T * N;
     const int red_k = std::max(N / kFftCols, 32);
     if ((st = proj_alloc(p, (void**)&p.proj_shift, sh.size() * sizeof(int4), "projection shifts")) != PROP_OK) return st;
     if ((st = proj_alloc(p, (void**)&p.proj_mask, mask.size(), "blade masks")) != PROP_OK) return st;
@@ -307,8 +357,8 @@ const uint8_t* blade_mask(const Plan& p, int b) { return p.proj_mask + (size_t)b
 
 // Z = M_b U P_b V_t(b) into z (or, with `loss`, the data term and its k-space gradient into p.proj_kg).
 prop_status proj_forward_impl(Plan& p, int b, const float2* V, float2* z, const CartLoss* loss, cudaStream_t s) {
-  const long pix = (long)p.N * p.N;
-  const unsigned blocks = (unsigned)((pix + kProjThreads / 32 - 1) / (kProjThreads / 32));
+  const long warps = (long)p.N * p.N / kProjPix;
+  const unsigned blocks = (unsigned)((warps + kProjThreads / 32 - 1) / (kProjThreads / 32));
   PROJ_TRY(launch_dep(proj_image_kernel, dim3(blocks), dim3(kProjThreads), 0, s, V, blade_shifts(p, b), p.N, p.Nf,
                       p.blade_frame[b], p.proj_img));
   PROJ_TRY(cart_fft_pass(p.N, kCartRowsFwd, p.proj_img, p.proj_k, p.proj_twiddle, nullptr, nullptr, 1.f, s));
@@ -400,7 +450,8 @@ prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev, const v
   PROJ_TRY(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
   float2* cur = (float2*)V_dev;
   float2* nxt = p.vol2;
-  const int ublocks = update_blocks(p);
+  const dim3 ugrid((unsigned)update_row_blocks(p), (unsigned)(p.T * p.N));
+  if ((long)ugrid.x * ugrid.y > p.red_proj_u.capacity) return fail(PROP_ERR_INVALID_ARG, "proj_reconstruct: reduction capacity");
   for (int k = 1; k <= q.iters; ++k) {
     const int b = (k - 1) % p.B;
     CartLoss loss{};
@@ -441,7 +492,10 @@ prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev, const v
     u.counter = p.red_proj_u.counter;
     u.data_loss = p.scalars + 3;
     u.loss_out = p.loss_dev + (k - 1);
-    PROJ_TRY(launch_dep(proj_update_kernel, dim3((unsigned)ublocks), dim3(kProjThreads), 0, s, u));
+    if (p.T > 1 && q.tv_t != 0.f)
+      PROJ_TRY(launch_dep(proj_update_kernel<true>, ugrid, dim3(kProjThreads), 0, s, u));
+    else
+      PROJ_TRY(launch_dep(proj_update_kernel<false>, ugrid, dim3(kProjThreads), 0, s, u));
     std::swap(cur, nxt);
   }
   if (cur != (float2*)V_dev) PROJ_TRY(cudaMemcpyAsync(V_dev, cur, vbytes, cudaMemcpyDeviceToDevice, s));

@@ -79,7 +79,7 @@ typedef struct prop_plan_s* prop_plan;
 /* Problem geometry.  All arrays are host memory, read during plan creation
  * only (the plan keeps its own copies). */
 typedef struct prop_plan_desc {
-  int n;                  /* image size N: multiple of 8, 8 <= N <= 512, 2N = 2^a 3^b */
+  int n;                  /* image size N: multiple of 8, 16 <= N <= 512, 2N = 2^a 3^b */
   int nf;                 /* spectral bins Nf >= 1 */
   const double* delta;    /* [nf] displacement Delta_f of each bin, pixels along readout */
   int nblades;            /* B >= 1 */
@@ -95,8 +95,8 @@ typedef struct prop_plan_desc {
   int row_kernel;         /* row kernel of prop_reconstruct / prop_recon_step (single bin chunk):
                              0 = auto, 1 = one CTA per (image row, 16 bins),
                              2 = persistent warp-specialised (the update of one row overlaps
-                             the row FFTs of its neighbours; needs 2N <= 512, 2N != 16 and a bin
-                             stride that is a multiple of 16, else plan creation fails).
+                             the row FFTs of its neighbours; needs 2N <= 512 and a bin stride
+                             that is a multiple of 16, else plan creation fails).
                              Auto takes 2 when it is possible and there are at least 8
                              (row, 16-bin) units per SM, else 1.  Same iterates either way. */
   int device;             /* CUDA device ordinal */

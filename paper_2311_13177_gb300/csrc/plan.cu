@@ -224,9 +224,9 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   if (!d || !out) return fail(PROP_ERR_INVALID_ARG, "plan_create: null argument");
   *out = nullptr;
   const int N = d->n;
-  if (N < 8 || N > 512 || N % 8 != 0 || !fft_size_supported(2 * N))
+  if (N < 16 || N > 512 || N % 8 != 0 || !fft_size_supported(2 * N))
     return fail(PROP_ERR_INVALID_ARG,
-                "plan_create: n must be a multiple of 8 in [8, 512] with 2n = 2^a 3^b (n = " +
+                "plan_create: n must be a multiple of 8 in [16, 512] with 2n = 2^a 3^b (n = " +
                     std::to_string(N) + ")");
   if (d->nf < 1 || d->nf > 4096) return fail(PROP_ERR_INVALID_ARG, "plan_create: nf out of range");
   if (d->nblades < 1 || d->lines < 1 || d->readout < 1)
@@ -638,7 +638,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   if (p->row_kernel == 2 && !p->fused_ws) {
     plan_free(p);
     return fail(PROP_ERR_INVALID_ARG,
-                "plan_create: row_kernel 2 needs 2N <= 512, 2N != 16, one bin chunk and a bin stride that is a "
+                "plan_create: row_kernel 2 needs 2N <= 512, one bin chunk and a bin stride that is a "
                 "multiple of 16");
   }
   {

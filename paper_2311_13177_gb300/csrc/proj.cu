@@ -346,12 +346,6 @@ prop_status plan_ensure_proj(Plan& p, bool images) {
 
 namespace {
 
-#define PROJ_TRY(call)                                      \
-  do {                                                      \
-    cudaError_t e__ = (call);                               \
-    if (e__ != cudaSuccess) return cuda_fail(e__, #call);   \
-  } while (0)
-
 const int4* blade_shifts(const Plan& p, int b) { return p.proj_shift + (size_t)b * p.Nf; }
 const uint8_t* blade_mask(const Plan& p, int b) { return p.proj_mask + (size_t)b * p.N * p.N; }
 
@@ -359,18 +353,18 @@ const uint8_t* blade_mask(const Plan& p, int b) { return p.proj_mask + (size_t)b
 prop_status proj_forward_impl(Plan& p, int b, const float2* V, float2* z, const CartLoss* loss, cudaStream_t s) {
   const long warps = (long)p.N * p.N / kProjPix;
   const unsigned blocks = (unsigned)((warps + kProjThreads / 32 - 1) / (kProjThreads / 32));
-  PROJ_TRY(launch_dep(proj_image_kernel, dim3(blocks), dim3(kProjThreads), 0, s, V, blade_shifts(p, b), p.N, p.Nf,
+  PROP_CUDA(launch_dep(proj_image_kernel, dim3(blocks), dim3(kProjThreads), 0, s, V, blade_shifts(p, b), p.N, p.Nf,
                       p.blade_frame[b], p.proj_img));
-  PROJ_TRY(cart_fft_pass(p.N, kCartRowsFwd, p.proj_img, p.proj_k, p.proj_twiddle, nullptr, nullptr, 1.f, s));
-  PROJ_TRY(cart_fft_pass(p.N, kCartColsFwd, p.proj_k, loss ? p.proj_kg : z, p.proj_twiddle, blade_mask(p, b), loss,
+  PROP_CUDA(cart_fft_pass(p.N, kCartRowsFwd, p.proj_img, p.proj_k, p.proj_twiddle, nullptr, nullptr, 1.f, s));
+  PROP_CUDA(cart_fft_pass(p.N, kCartColsFwd, p.proj_k, loss ? p.proj_kg : z, p.proj_twiddle, blade_mask(p, b), loss,
                          1.f / (float)p.N, s));
   return PROP_OK;
 }
 
 // g = U^H M_b z (image space) into p.proj_g.
 prop_status proj_kadjoint_impl(Plan& p, int b, const float2* z, cudaStream_t s) {
-  PROJ_TRY(cart_fft_pass(p.N, kCartColsInv, z, p.proj_k, p.proj_twiddle, blade_mask(p, b), nullptr, 1.f, s));
-  PROJ_TRY(cart_fft_pass(p.N, kCartRowsInv, p.proj_k, p.proj_g, p.proj_twiddle, nullptr, nullptr, 1.f / (float)p.N, s));
+  PROP_CUDA(cart_fft_pass(p.N, kCartColsInv, z, p.proj_k, p.proj_twiddle, blade_mask(p, b), nullptr, 1.f, s));
+  PROP_CUDA(cart_fft_pass(p.N, kCartRowsInv, p.proj_k, p.proj_g, p.proj_twiddle, nullptr, nullptr, 1.f / (float)p.N, s));
   return PROP_OK;
 }
 
@@ -414,7 +408,7 @@ prop_status prop_proj_adjoint(prop_plan plan, int blade, const void* z_dev, void
   if (st != PROP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = proj_kadjoint_impl(p, blade, (const float2*)z_dev, s)) != PROP_OK) return st;
-  PROJ_TRY(launch_dep(proj_adjoint_kernel, dim3((unsigned)(8 * p.num_sms)), dim3(kProjThreads), 0, s,
+  PROP_CUDA(launch_dep(proj_adjoint_kernel, dim3((unsigned)(8 * p.num_sms)), dim3(kProjThreads), 0, s,
                       (const float2*)p.proj_g, blade_shifts(p, blade), p.N, p.Nf, p.T, p.blade_frame[blade],
                       (float2*)V_dev));
   return PROP_OK;
@@ -438,16 +432,16 @@ prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev, const v
   if (img_dev) {
     // U img_b for every blade, and the image term's constant outside each mask
     for (int b = 0; b < p.B; ++b) {
-      PROJ_TRY(cart_fft_pass(p.N, kCartRowsFwd, (const float2*)img_dev + b * n2, p.proj_k, p.proj_twiddle, nullptr,
+      PROP_CUDA(cart_fft_pass(p.N, kCartRowsFwd, (const float2*)img_dev + b * n2, p.proj_k, p.proj_twiddle, nullptr,
                              nullptr, 1.f, s));
-      PROJ_TRY(cart_fft_pass(p.N, kCartColsFwd, p.proj_k, p.proj_yimg + b * n2, p.proj_twiddle, nullptr, nullptr,
+      PROP_CUDA(cart_fft_pass(p.N, kCartColsFwd, p.proj_k, p.proj_yimg + b * n2, p.proj_twiddle, nullptr, nullptr,
                              1.f / (float)p.N, s));
     }
-    PROJ_TRY(launch_dep(proj_const_kernel, dim3((unsigned)p.B), dim3(kProjThreads), 0, s,
+    PROP_CUDA(launch_dep(proj_const_kernel, dim3((unsigned)p.B), dim3(kProjThreads), 0, s,
                         (const float2*)p.proj_yimg, (const uint8_t*)p.proj_mask, p.N, q.w_image, p.proj_const));
   }
-  PROJ_TRY(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
-  PROJ_TRY(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
+  PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
+  PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
   float2* cur = (float2*)V_dev;
   float2* nxt = p.vol2;
   const dim3 ugrid((unsigned)update_row_blocks(p), (unsigned)(p.T * p.N));
@@ -493,15 +487,15 @@ prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev, const v
     u.data_loss = p.scalars + 3;
     u.loss_out = p.loss_dev + (k - 1);
     if (p.T > 1 && q.tv_t != 0.f)
-      PROJ_TRY(launch_dep(proj_update_kernel<true>, ugrid, dim3(kProjThreads), 0, s, u));
+      PROP_CUDA(launch_dep(proj_update_kernel<true>, ugrid, dim3(kProjThreads), 0, s, u));
     else
-      PROJ_TRY(launch_dep(proj_update_kernel<false>, ugrid, dim3(kProjThreads), 0, s, u));
+      PROP_CUDA(launch_dep(proj_update_kernel<false>, ugrid, dim3(kProjThreads), 0, s, u));
     std::swap(cur, nxt);
   }
-  if (cur != (float2*)V_dev) PROJ_TRY(cudaMemcpyAsync(V_dev, cur, vbytes, cudaMemcpyDeviceToDevice, s));
+  if (cur != (float2*)V_dev) PROP_CUDA(cudaMemcpyAsync(V_dev, cur, vbytes, cudaMemcpyDeviceToDevice, s));
   if (loss_trace_host && q.iters > 0) {
-    PROJ_TRY(cudaMemcpyAsync(loss_trace_host, p.loss_dev, sizeof(double) * q.iters, cudaMemcpyDeviceToHost, s));
-    PROJ_TRY(cudaStreamSynchronize(s));
+    PROP_CUDA(cudaMemcpyAsync(loss_trace_host, p.loss_dev, sizeof(double) * q.iters, cudaMemcpyDeviceToHost, s));
+    PROP_CUDA(cudaStreamSynchronize(s));
   }
   return PROP_OK;
 }

@@ -38,7 +38,7 @@ def test_binding_covers_every_declared_symbol():
 def test_invalid_sizes_are_rejected_before_any_device_work(libprop):
     from paper_2311_13177_gb300.serve import plan_desc
     from paper_2311_13177_gb300._lib import PROP_OK
-    for N in (7, 12, 40, 1000):   # not a multiple of 8, or 2N not 2^a 3^b, or too large
+    for N in (7, 8, 12, 40, 1000):   # not a multiple of 8, below 16, 2N not 2^a 3^b, or too large
         d, keep = plan_desc(N, 4, N, [0.0], [0.0])
         h = ctypes.c_void_p()
         st = libprop.prop_plan_create(ctypes.byref(d), ctypes.byref(h))

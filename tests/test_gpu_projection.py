@@ -92,10 +92,10 @@ def test_reconstruction_matches_oracle(with_image):
     assert tro[-4:].sum() < tro[:4].sum()
 
 
-def test_projection_model_rejects_tiny_images():
+def test_blade_index_is_checked():
     from paper_2311_13177_gb300._lib import PropError
-    theta, delta, frames, V = _case(8, 2, 2, 4, 8, 1, seed=3)
-    plan = _plan(8, 4, 8, theta, delta, frames, 1)
+    theta, delta, frames, V = _case(16, 2, 2, 4, 16, 1, seed=3)
+    plan = _plan(16, 4, 16, theta, delta, frames, 1)
     with pytest.raises(PropError):
-        plan.proj_forward(0, torch.from_numpy(V).cuda())
+        plan.proj_forward(2, torch.from_numpy(V).cuda())
     plan.destroy()

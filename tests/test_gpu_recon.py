@@ -161,11 +161,12 @@ def test_warp_specialised_reconstruct_equals_step_sequence():
     assert np.array_equal(np.array(trs), tr)
 
 
-@pytest.mark.parametrize("shape", [(8, 16, 2, 4, 8), (32, 8, 3, 4, 32)])
+@pytest.mark.parametrize("shape", [(32, 8, 3, 4, 32), (32, 4, 2, 4, 32)])
 def test_warp_specialised_row_kernel_rejected_where_impossible(shape):
-    """2N = 16 (a 16-thread transform group) and a bin stride of 8 cannot run it."""
+    """Bin strides of 8 and 4 (less than the 16-bin unit) cannot run it."""
     from paper_2311_13177_gb300._lib import PropError
     N, Nf, B, L, R = shape
     c = random_case(N, Nf, B, L, R, seed=3)
     with pytest.raises(PropError):
         _row_kernel_plan(c, 1, 2)
+

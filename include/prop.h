@@ -338,6 +338,15 @@ PROP_API prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev
                                            const prop_proj_params* params, void* V_dev, double* loss_trace_host,
                                            void* stream);
 
+/* The results section's baseline (Sec. 6): the coverage-weighted average of
+ * blades blade_lo .. blade_hi-1 in k-space (each Cartesian cell averages
+ * the blades whose mask holds it; uncovered cells are zero), then the
+ * inverse DFT.  ycart_dev [B][N][N]; img_dev [N][N].  All blades for a
+ * static series; the most recent ones before a frame for a dynamic one.
+ * Does not synchronise. */
+PROP_API prop_status prop_proj_baseline(prop_plan plan, const void* ycart_dev, int blade_lo, int blade_hi,
+                                        void* img_dev, void* stream);
+
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 PROP_API const char* prop_last_error(void);
 

@@ -36,7 +36,10 @@ Readings where the paper is silent:
     forward difference, and L1 sparsity l1 * sum sqrt(|V|^2 + eps^2);
   * schedule: iteration k (1-based) uses blade (k - 1) mod B; Adam as in
     ``recon.adam_step``; V_0 = 0; loss_trace[k - 1] is the iteration's loss
-    before its update.
+    before its update;
+  * baseline (Sec. 6): the coverage-weighted k-space average of a range of
+    blades (all blades, or the most recent ones of a dynamic series), each
+    cell averaging the blades whose mask holds it, then the inverse DFT.
 """
 from __future__ import annotations
 
@@ -172,6 +175,20 @@ def adjoint(z: np.ndarray, g: Geometry, b: int) -> np.ndarray:
 def image_of(ycart: np.ndarray, g: Geometry, b: int) -> np.ndarray:
     """The measured image of blade b when none is given: U^H (M_b ycart_b)."""
     return idft(np.asarray(ycart[b], dtype=np.complex128) * blade_mask(g.N, float(g.theta[b]), g.L, g.R))
+
+
+def baseline(ycart: np.ndarray, g: Geometry, lo: int = 0, hi=None) -> np.ndarray:
+    """The results section's baseline: the coverage-weighted average of the
+    blades lo .. hi-1 in k-space (each Cartesian cell averages the blades
+    whose mask holds it; uncovered cells are zero), then the inverse DFT."""
+    hi = g.B if hi is None else hi
+    acc = np.zeros((g.N, g.N), dtype=np.complex128)
+    cnt = np.zeros((g.N, g.N))
+    for b in range(lo, hi):
+        m = blade_mask(g.N, float(g.theta[b]), g.L, g.R)
+        acc += m * np.asarray(ycart[b], dtype=np.complex128)
+        cnt += m
+    return idft(np.where(cnt > 0, acc / np.maximum(cnt, 1.0), 0.0))
 
 
 def l1(V: np.ndarray, eps: float):

@@ -77,6 +77,7 @@ SIGNATURES = {
     "prop_proj_adjoint": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "prop_proj_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(ProjParamsC), c_void_p,
                                       ctypes.POINTER(c_double), c_void_p]),
+    "prop_proj_baseline": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "prop_check_bounded_wait": (c_int, [c_int, ctypes.c_longlong, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "prop_last_error": (ctypes.c_char_p, []),
 }

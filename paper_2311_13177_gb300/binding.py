@@ -253,6 +253,18 @@ class Plan:
               "prop_proj_reconstruct")
         return V, (tr[:params.iters] if trace else None)
 
+    def proj_baseline(self, ycart: torch.Tensor, blade_lo: int = 0, blade_hi: int = None,
+                      out: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """Coverage-weighted k-space average of blades [blade_lo, blade_hi), inverse DFT: [N, N]."""
+        if blade_hi is None:
+            blade_hi = self.B
+        if out is None:
+            out = torch.empty((self.N, self.N), dtype=torch.complex64, device=ycart.device)
+        check(lib().prop_proj_baseline(self.handle, _dev_ptr(ycart, (self.B, self.N, self.N), "ycart"),
+                                       int(blade_lo), int(blade_hi), _dev_ptr(out, (self.N, self.N), "image"),
+                                       _stream(stream)), "prop_proj_baseline")
+        return out
+
     def profile_enable(self, on: bool = True) -> None:
         check(lib().prop_profile_enable(self.handle, 1 if on else 0), "prop_profile_enable")
 

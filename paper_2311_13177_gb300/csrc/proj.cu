@@ -246,6 +246,28 @@ __global__ void __launch_bounds__(kProjThreads) proj_const_kernel(const float2* 
   if (threadIdx.x == 0) c[blockIdx.x] = (double)wi * s;
 }
 
+// Coverage-weighted k-space average of blades lo .. hi-1: each cell averages
+// the blades whose mask holds it (zero where none does).
+__global__ void __launch_bounds__(kProjThreads) proj_baseline_kernel(const float2* __restrict__ y,
+                                                                     const uint8_t* __restrict__ mask, int N, int lo,
+                                                                     int hi, float2* __restrict__ out) {
+  grid_dep_wait();
+  grid_dep_release();
+  const size_t n2 = (size_t)N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    float sx = 0.f, sy = 0.f;
+    int c = 0;
+    for (int b = lo; b < hi; ++b)
+      if (mask[b * n2 + i]) {
+        const float2 v = y[b * n2 + i];
+        sx += v.x;
+        sy += v.y;
+        ++c;
+      }
+    out[i] = c > 0 ? make_float2(sx / (float)c, sy / (float)c) : make_float2(0.f, 0.f);
+  }
+}
+
 // Blocks per image row of the update: about 8 voxels a thread, at most 4.
 int update_row_blocks(const Plan& p) {
   const int rl = p.N * p.Nf;
@@ -411,6 +433,24 @@ prop_status prop_proj_adjoint(prop_plan plan, int blade, const void* z_dev, void
   PROP_CUDA(launch_dep(proj_adjoint_kernel, dim3((unsigned)(8 * p.num_sms)), dim3(kProjThreads), 0, s,
                       (const float2*)p.proj_g, blade_shifts(p, blade), p.N, p.Nf, p.T, p.blade_frame[blade],
                       (float2*)V_dev));
+  return PROP_OK;
+}
+
+prop_status prop_proj_baseline(prop_plan plan, const void* ycart_dev, int blade_lo, int blade_hi, void* img_dev,
+                               void* stream) {
+  if (!plan || !ycart_dev || !img_dev) return fail(PROP_ERR_INVALID_ARG, "proj_baseline: null argument");
+  Plan& p = *plan->p;
+  if (blade_lo < 0 || blade_hi > p.B || blade_lo >= blade_hi)
+    return fail(PROP_ERR_INVALID_ARG, "proj_baseline: need 0 <= blade_lo < blade_hi <= B");
+  DeviceGuard g(p.device);
+  prop_status st = plan_ensure_proj(p, false);
+  if (st != PROP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  PROP_CUDA(launch_dep(proj_baseline_kernel, dim3((unsigned)(4 * p.num_sms)), dim3(kProjThreads), 0, s,
+                       (const float2*)ycart_dev, (const uint8_t*)p.proj_mask, p.N, blade_lo, blade_hi, p.proj_kg));
+  PROP_CUDA(cart_fft_pass(p.N, kCartColsInv, p.proj_kg, p.proj_k, p.proj_twiddle, nullptr, nullptr, 1.f, s));
+  PROP_CUDA(cart_fft_pass(p.N, kCartRowsInv, p.proj_k, (float2*)img_dev, p.proj_twiddle, nullptr, nullptr,
+                          1.f / (float)p.N, s));
   return PROP_OK;
 }
 

@@ -99,3 +99,17 @@ def test_blade_index_is_checked():
     with pytest.raises(PropError):
         plan.proj_forward(2, torch.from_numpy(V).cuda())
     plan.destroy()
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 4), (1, 3)])
+def test_baseline_matches_oracle(lo, hi):
+    N, Nf, B, L, R, T = 32, 2, 4, 8, 32, 1
+    theta, delta, frames, _ = _case(N, Nf, B, L, R, T, seed=31)
+    g = make_geometry(N, L, R, theta, delta, frames, T)
+    rng = np.random.default_rng(32)
+    ycart = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
+    plan = _plan(N, L, R, theta, delta, frames, T)
+    img = plan.proj_baseline(torch.from_numpy(ycart).cuda(), lo, hi).cpu().numpy()
+    plan.destroy()
+    ref = pj.baseline(ycart.astype(np.complex128), g, lo, hi)
+    assert rel(img, ref) < TOL

@@ -192,3 +192,29 @@ def test_reconstruction_fits_blade_data_of_a_known_volume():
     p = pj.ProjParams(iters=40, lr=0.05, tv_xy=0.0)
     V, tr = pj.reconstruct(ycart, None, g, p)
     assert tr[-4:].sum() < 0.2 * tr[:4].sum()
+
+
+def test_baseline_of_one_blade_is_its_image():
+    rng = np.random.default_rng(11)
+    N = 12
+    g = make_geometry(N, 4, 8, [0.4, 1.3], [0.0])
+    ycart = _rand_c(rng, (2, N, N))
+    assert np.allclose(pj.baseline(ycart, g, 1, 2), pj.image_of(ycart, g, 1), atol=1e-12)
+
+
+def test_baseline_averages_overlapping_blades():
+    """Blades whose data agree give that data on the union of their masks;
+    where only one blade covers a cell its value is kept, where two do the
+    mean of the two."""
+    rng = np.random.default_rng(12)
+    N = 16
+    g = make_geometry(N, 6, 12, [0.0, np.pi / 2], [0.0])
+    y = _rand_c(rng, (N, N))
+    z = _rand_c(rng, (N, N))
+    m0 = pj.blade_mask(N, 0.0, 6, 12)
+    m1 = pj.blade_mask(N, np.pi / 2, 6, 12)
+    same = pj.dft(pj.baseline(np.stack([y, y]), g))
+    assert np.allclose(same, y * (m0 | m1), atol=1e-12)
+    mix = pj.dft(pj.baseline(np.stack([y, z]), g))
+    ref = np.where(m0 & m1, 0.5 * (y + z), np.where(m0, y, np.where(m1, z, 0)))
+    assert np.allclose(mix, ref, atol=1e-12)

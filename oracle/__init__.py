@@ -16,6 +16,10 @@ Contents
   recon     data-consistency loss, smoothed TV in x-y and in time, Adam, and
             the full-batch reconstruction loop (Sec. 4.3), plus the phi = 0
             render and the fat/water split (Sec. 4.3, Sec. 6)
+  kplanes   the dynamic K-Planes volume model (Sec. 4.1, Eq. 3): six planes
+            of feature vectors, bilinear lookups, Hadamard product, weighting
+            vector, two scales; rendering on the volume grid and the
+            parameter gradients
   projection  the paper's own forward model (Sec. 4.2): interpolated
             projection at the blade's tilt, centred DFT and blade mask; its
             adjoint; the image- plus k-space loss with TV (x-y, spectral,
@@ -32,9 +36,10 @@ from .ndft import forward, adjoint, forward_at, adjoint_at
 from .recon import (ReconParams, data_loss, tv_xy, tv_t, loss_and_grad,
                     adam_step, reconstruct, render)
 from . import projection
+from . import kplanes
 
 __all__ = [
     "Geometry", "make_geometry", "sample_coords", "phase_table", "forward", "adjoint",
     "forward_at", "adjoint_at", "ReconParams", "data_loss", "tv_xy", "tv_t",
-    "loss_and_grad", "adam_step", "reconstruct", "render", "projection",
+    "loss_and_grad", "adam_step", "reconstruct", "render", "projection", "kplanes",
 ]

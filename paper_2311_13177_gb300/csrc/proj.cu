@@ -274,8 +274,9 @@ int update_row_blocks(const Plan& p) {
   return std::max(1, std::min(4, rl / (8 * kProjThreads)));
 }
 
+// Allocates *ptr unless a previous, interrupted set-up already did.
 prop_status proj_alloc(Plan& p, void** ptr, size_t bytes, const char* what) {
-  *ptr = nullptr;
+  if (*ptr) return PROP_OK;
   cudaError_t e = plan_dev_alloc(&p, ptr, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     cudaGetLastError();

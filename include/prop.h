@@ -323,7 +323,8 @@ typedef struct prop_proj_params {
  * PROP_ERR_OOM, PROP_ERR_CUDA.  Does not synchronise. */
 PROP_API prop_status prop_proj_forward(prop_plan plan, int blade, const void* V_dev, void* z_dev, void* stream);
 /* V = P_b^H U^H M_b z: frame t(b) of the volume gets the transposed
- * projection, the other frames zero.  Does not synchronise. */
+ * projection, the other frames zero.  Errors as prop_proj_forward.  Does
+ * not synchronise. */
 PROP_API prop_status prop_proj_adjoint(prop_plan plan, int blade, const void* z_dev, void* V_dev, void* stream);
 /* Adam over the blades in turn (Sec. 4.3) on
  *   w_kspace sum_{M_b} |Z - ycart_b|^2 + w_image sum |U^H M_b Z - img_b|^2
@@ -334,6 +335,9 @@ PROP_API prop_status prop_proj_adjoint(prop_plan plan, int blade, const void* z_
  * V_dev: the start in, the result out.  loss_trace_host (may be NULL):
  * [iters] loss of each iteration's blade before its update.  Synchronises
  * only when a trace is requested. */
+/* Errors: PROP_ERR_INVALID_ARG (null plan/ycart/V, iters < 0, Adam
+ * parameters out of range, a negative or non-finite weight, tv_eps <= 0),
+ * PROP_ERR_OOM (optimiser state, image spectra), PROP_ERR_CUDA. */
 PROP_API prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev, const void* img_dev,
                                            const prop_proj_params* params, void* V_dev, double* loss_trace_host,
                                            void* stream);
@@ -343,7 +347,8 @@ PROP_API prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev
  * the blades whose mask holds it; uncovered cells are zero), then the
  * inverse DFT.  ycart_dev [B][N][N]; img_dev [N][N].  All blades for a
  * static series; the most recent ones before a frame for a dynamic one.
- * Does not synchronise. */
+ * Errors: PROP_ERR_INVALID_ARG (null, not 0 <= blade_lo < blade_hi <= B),
+ * PROP_ERR_OOM, PROP_ERR_CUDA.  Does not synchronise. */
 PROP_API prop_status prop_proj_baseline(prop_plan plan, const void* ycart_dev, int blade_lo, int blade_hi,
                                         void* img_dev, void* stream);
 

@@ -352,6 +352,37 @@ PROP_API prop_status prop_proj_reconstruct(prop_plan plan, const void* ycart_dev
 PROP_API prop_status prop_proj_baseline(prop_plan plan, const void* ycart_dev, int blade_lo, int blade_hi,
                                         void* img_dev, void* stream);
 
+/* ---- The dynamic K-Planes volume model (Sec. 4.1, Eq. 3) ----------------
+ *
+ * V(x, y, omega, t) = sum over scales s < scales of sum_k a_s,k
+ * prod_c psi(p_s,c, pi_c(x, y, omega, t))_k, the six planes c = xy, x-omega,
+ * x-t, y-omega, y-t, omega-t holding `features` (1..16) complex features per
+ * node, interpolated bilinearly with cell-centred nodes (voxel i maps to
+ * (i + 1/2) R / N - 1/2 on a spatial axis of R nodes, clamped to [0, R-1];
+ * spectral and time indices are nodes).  Scale s has N >> s spatial nodes
+ * (scales is 1 or 2).  Parameters: one complex64 device buffer, per scale in
+ * order xy [n][n][F], xw [Nf][n][F], xt [T][n][F], yw [Nf][n][F],
+ * yt [T][n][F], wt [T][Nf][F], then a [F]. */
+/* Number of complex parameters of that layout. */
+PROP_API prop_status prop_kplanes_param_count(prop_plan plan, int features, int scales, size_t* count);
+/* V_dev [T][N][N][Nf] = the model rendered on the volume grid.  Does not synchronise. */
+PROP_API prop_status prop_kplanes_render(prop_plan plan, int features, int scales, const void* params_dev,
+                                         void* V_dev, void* stream);
+/* grad_dev (same layout as the parameters) = dL/dRe z + i dL/dIm z for every
+ * parameter z, given gV_dev = dL/dRe V + i dL/dIm V.  Sums are accumulated
+ * with atomics (order not fixed).  Does not synchronise. */
+PROP_API prop_status prop_kplanes_vjp(prop_plan plan, int features, int scales, const void* params_dev,
+                                      const void* gV_dev, void* grad_dev, void* stream);
+/* Adam on the model's parameters (in place) for the loss of prop_reconstruct
+ * (non-uniform data term + TV of the rendered volume): per iteration render,
+ * loss and grad V, transpose, Adam.  loss_trace_host as in prop_reconstruct.
+ * Allocates and frees Adam state for the parameters; synchronises.  Errors:
+ * PROP_ERR_INVALID_ARG (null, features/scales out of range, parameters out of
+ * range), PROP_ERR_OOM, PROP_ERR_CUDA. */
+PROP_API prop_status prop_kplanes_reconstruct(prop_plan plan, const void* y_dev, const prop_recon_params* params,
+                                              int features, int scales, void* kp_params_dev, double* loss_trace_host,
+                                              void* stream);
+
 /* Message for the last non-OK status returned on the calling thread ("" if none). */
 PROP_API const char* prop_last_error(void);
 

@@ -165,3 +165,27 @@ def loss_and_grad(params: dict, y: np.ndarray, g, p):
     V = render(params, g.N, g.Nf, g.T)
     loss, gV = volume_loss(V, y, g, p)
     return loss, vjp(params, gV, g.N, g.Nf, g.T)
+
+
+def reconstruct(y: np.ndarray, g, p, params0: dict):
+    """Adam on every parameter array (``recon.adam_step``, step k for all)
+    for ``loss_and_grad``: returns (params_K, loss_trace[K])."""
+    from .recon import adam_step
+    prm = {"planes": [{c: np.array(v, dtype=np.complex128) for c, v in d.items()} for d in params0["planes"]],
+           "a": [np.array(v, dtype=np.complex128) for v in params0["a"]]}
+    mom = {"planes": [{c: [np.zeros(v.shape + (2,)), np.zeros(v.shape + (2,))] for c, v in d.items()}
+                      for d in prm["planes"]],
+           "a": [[np.zeros(v.shape + (2,)), np.zeros(v.shape + (2,))] for v in prm["a"]]}
+    trace = np.zeros(p.iters)
+    for k in range(1, p.iters + 1):
+        loss, G = loss_and_grad(prm, y, g, p)
+        trace[k - 1] = loss
+        for s in range(len(prm["planes"])):
+            for c in PLANES:
+                mm, vv = mom["planes"][s][c]
+                prm["planes"][s][c], mm, vv = adam_step(prm["planes"][s][c], G["planes"][s][c], mm, vv, k, p)
+                mom["planes"][s][c] = [mm, vv]
+            mm, vv = mom["a"][s]
+            prm["a"][s], mm, vv = adam_step(prm["a"][s], G["a"][s], mm, vv, k, p)
+            mom["a"][s] = [mm, vv]
+    return prm, trace

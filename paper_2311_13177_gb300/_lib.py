@@ -78,6 +78,11 @@ SIGNATURES = {
     "prop_proj_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(ProjParamsC), c_void_p,
                                       ctypes.POINTER(c_double), c_void_p]),
     "prop_proj_baseline": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "prop_kplanes_param_count": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_size_t)]),
+    "prop_kplanes_render": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "prop_kplanes_vjp": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "prop_kplanes_reconstruct": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_int, c_int, c_void_p,
+                                         ctypes.POINTER(c_double), c_void_p]),
     "prop_check_bounded_wait": (c_int, [c_int, ctypes.c_longlong, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "prop_last_error": (ctypes.c_char_p, []),
 }

@@ -265,6 +265,47 @@ class Plan:
                                        _stream(stream)), "prop_proj_baseline")
         return out
 
+    def kplanes_param_count(self, features: int = 8, scales: int = 2) -> int:
+        n = ctypes.c_size_t()
+        check(lib().prop_kplanes_param_count(self.handle, int(features), int(scales), ctypes.byref(n)),
+              "prop_kplanes_param_count")
+        return int(n.value)
+
+    def _kp_ptr(self, t: torch.Tensor, features: int, scales: int, name: str) -> ctypes.c_void_p:
+        return _dev_ptr(t, (self.kplanes_param_count(features, scales),), name)
+
+    def kplanes_render(self, params: torch.Tensor, features: int = 8, scales: int = 2, V: torch.Tensor = None,
+                       stream=None) -> torch.Tensor:
+        """Render the K-Planes model (flat complex64 parameter tensor) on the volume grid."""
+        if V is None:
+            V = torch.empty(self.vol_shape, dtype=torch.complex64, device=params.device)
+        check(lib().prop_kplanes_render(self.handle, int(features), int(scales),
+                                        self._kp_ptr(params, features, scales, "params"),
+                                        _dev_ptr(V, self.vol_shape, "V"), _stream(stream)), "prop_kplanes_render")
+        return V
+
+    def kplanes_vjp(self, params: torch.Tensor, gV: torch.Tensor, features: int = 8, scales: int = 2,
+                    grad: torch.Tensor = None, stream=None) -> torch.Tensor:
+        if grad is None:
+            grad = torch.empty_like(params)
+        check(lib().prop_kplanes_vjp(self.handle, int(features), int(scales),
+                                     self._kp_ptr(params, features, scales, "params"),
+                                     _dev_ptr(gV, self.vol_shape, "gV"),
+                                     self._kp_ptr(grad, features, scales, "grad"), _stream(stream)),
+              "prop_kplanes_vjp")
+        return grad
+
+    def kplanes_reconstruct(self, y: torch.Tensor, params: ReconParams, kp: torch.Tensor, features: int = 8,
+                            scales: int = 2, stream=None):
+        """Adam on the K-Planes parameters kp (in place); returns (kp, loss_trace)."""
+        tr = np.zeros(max(params.iters, 1), dtype=np.float64)
+        pc = params.c()
+        check(lib().prop_kplanes_reconstruct(self.handle, _dev_ptr(y, self.data_shape, "y"), ctypes.byref(pc),
+                                             int(features), int(scales), self._kp_ptr(kp, features, scales, "kp"),
+                                             tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)),
+              "prop_kplanes_reconstruct")
+        return kp, tr[:params.iters]
+
     def profile_enable(self, on: bool = True) -> None:
         check(lib().prop_profile_enable(self.handle, 1 if on else 0), "prop_profile_enable")
 

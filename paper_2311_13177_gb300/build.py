@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "libprop.so")
-SOURCES = ["plan.cu", "fft.cu", "nufft.cu", "optim.cu", "api.cu", "serve.cu", "peak.cu", "proj.cu"]
+SOURCES = ["plan.cu", "fft.cu", "nufft.cu", "optim.cu", "api.cu", "serve.cu", "peak.cu", "proj.cu", "kplanes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(HERE, "..", "include")]

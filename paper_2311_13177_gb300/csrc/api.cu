@@ -211,6 +211,16 @@ prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* 
 
 }  // namespace
 
+prop_status loss_grad_device(Plan& p, const float2* y, const AdamArgs& a, const float2* V, float2* grad,
+                             double* loss_out, cudaStream_t s) {
+  prop_status st;
+  if ((st = forward_impl(p, V, p.resid, y, &p.red_interp, p.scalars, s)) != PROP_OK) return st;
+  if ((st = adjoint_impl(p, p.resid, p.grad, true, s)) != PROP_OK) return st;
+  StageScope sc(p, kStOpt, s);
+  PROP_LAUNCH(tv_grad(p, V, p.grad, grad, a, &p.red_tv, p.scalars, loss_out, s));
+  return PROP_OK;
+}
+
 prop_status plan_step(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin, float2* Vout,
                       double* loss_dst, cudaStream_t s, bool rows_ready, bool next_rows) {
   return step_impl(p, y, q, k, Vin, Vout, loss_dst, s, rows_ready, next_rows);

@@ -224,6 +224,11 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters);
 // rows_ready: the plan's row workspace holds the forward row transform of Vin
 // (left by the previous step with next_rows); next_rows: leave the forward
 // row transform of Vout there.  Both only take effect with one bin chunk.
+struct AdamArgs;
+// Loss L(V) (data term + TV with a.tv_xy, a.tv_t, a.tv_eps; a.gscale = 2) into
+// *loss_out (device) and dL/dRe V + i dL/dIm V into grad (may be p.grad).
+prop_status loss_grad_device(Plan& p, const float2* y, const AdamArgs& a, const float2* V, float2* grad,
+                             double* loss_out, cudaStream_t s);
 prop_status plan_step(Plan& p, const float2* y, const prop_recon_params* q, int k, const float2* Vin,
                       float2* Vout, double* loss_dst, cudaStream_t s, bool rows_ready = false,
                       bool next_rows = false);

@@ -34,3 +34,35 @@ def workload_case(name):
     p = synth.make_problem(w)
     p.update(N=w.N, L=w.L, R=w.R, T=w.T)
     return w, p
+
+
+def kplanes_pack(params):
+    """Flat parameter vector in the C ABI's K-Planes layout (per scale: the six
+    planes in oracle order, then a)."""
+    from oracle.kplanes import PLANES
+    parts = []
+    for s in range(len(params["planes"])):
+        for c in PLANES:
+            parts.append(np.asarray(params["planes"][s][c]).reshape(-1))
+        parts.append(np.asarray(params["a"][s]).reshape(-1))
+    return np.concatenate(parts)
+
+
+def kplanes_unpack(flat, like):
+    """Inverse of ``kplanes_pack`` with the shapes of ``like``."""
+    from oracle.kplanes import PLANES
+    out = {"planes": [], "a": []}
+    o = 0
+    for s in range(len(like["planes"])):
+        d = {}
+        for c in PLANES:
+            sh = like["planes"][s][c].shape
+            n = int(np.prod(sh))
+            d[c] = np.asarray(flat[o:o + n]).reshape(sh)
+            o += n
+        out["planes"].append(d)
+        n = like["a"][s].size
+        out["a"].append(np.asarray(flat[o:o + n]))
+        o += n
+    assert o == len(flat)
+    return out

@@ -27,9 +27,10 @@ Contents
 
 Every function is pinned by a ``-m "not gpu"`` test against something other
 than itself (library special cases, closed forms, invariants, brute force,
-torch.optim.Adam); the full reconstruction trajectory is a composition of
-pinned parts and has no independent pin of its own (parity unpinned beyond
-that composition, as the paper prints no iterate values).
+torch.optim.Adam).  The three reconstruction loops (``recon.reconstruct``,
+``projection.reconstruct``, ``kplanes.reconstruct``) are pinned as wholes
+against independent torch statements of the same problems driven by
+torch.optim.Adam (iterates and loss traces to 1e-12).
 """
 from .geometry import Geometry, make_geometry, sample_coords, phase_table
 from .ndft import forward, adjoint, forward_at, adjoint_at

@@ -56,10 +56,18 @@ def parse():
     ap.add_argument("--no-projection", action="store_true",
                     help="skip the projection-model (the paper's own forward model) measurement")
     ap.add_argument("--bin-chunk", type=int, default=0, help="bins per grid pass (0: the plan's default)")
+    ap.add_argument("--kb-width", type=int, default=8, choices=[6, 8],
+                    help="Kaiser-Bessel width of the timed plan (8: the width whose reconstruction meets the "
+                         "1e-3 parity bar at the static workload; 6 drifts 2e-3 to 6e-3 from the exact operator's "
+                         "trajectory there)")
+    ap.add_argument("--no-kplanes", action="store_true", help="skip the K-Planes model measurement")
     ap.add_argument("--row-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="row kernel: 0 the plan's choice, 1 per-row CTAs, 2 warp-specialised")
     ap.add_argument("--diff-study", action="store_true",
                     help="differentiation workload: grid store vs recompute (memory and time), one JSON line")
+    ap.add_argument("--width-study", type=int, default=0, metavar="ITERS",
+                    help="reconstruct the --workload with kernel widths 6 and 8 for ITERS iterations and report "
+                         "how far the width-6 trajectory drifts from the width-8 one (one JSON line)")
     ap.add_argument("--workload", choices=["static", "dynamic", "diff"], default=WORKLOAD,
                     help="the headline line is the static workload; the others are for comparison")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -67,13 +75,13 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(w) -> dict:
+def workload_config(w, kb_width: int = 8) -> dict:
     kind = "static" if w.T == 1 else f"dynamic {w.T}-frame"
     opt = f"Adam lr {w.lr:g}, TV_xy {w.tv_xy:g}" + (f", TV_t {w.tv_t:g}" if w.tv_t else "")
     return {"workload": f"{kind} {w.N}x{w.N} image, {w.Nf} bins over [{w.delta_lo:g},{w.delta_hi:g}] px, "
                         f"{w.B} blades x {w.L} lines x {w.R} readout",
             "N": w.N, "Nf": w.Nf, "blades": w.B, "lines": w.L, "readout": w.R, "frames": w.T,
-            "oversampling": 2, "kb_width": 6, "optimizer": opt}
+            "oversampling": 2, "kb_width": kb_width, "optimizer": opt}
 
 
 def measured_peaks():
@@ -88,40 +96,58 @@ def measured_peaks():
 
 # --- oracle timing (CPU baseline and the reference arm) ------------------------
 
-def oracle_sample(bins: int = 8):
-    """The static problem restricted to its first `bins` of 32 spectral bins.
+SAMPLE_BLADES = 2
 
-    The oracle's work per iteration is linear in the bin count (every bin is
-    an independent exact sum of the same size), so a step on this sample
-    costs bins/32 of a full step."""
+
+def oracle_sample(blades: int = SAMPLE_BLADES):
+    """The static problem restricted to its first `blades` of 16 blades (all
+    32 bins, the full 256 x 256 x 32 volume).
+
+    The oracle's exact NDFT forward and explicit adjoint cost the same for
+    every sample, so their time on the sample scales to the full problem by
+    16 / blades exactly; the TV terms and the Adam step act on the whole
+    volume whatever the blade count, so their time is taken as measured."""
     import numpy as np
     import oracle
     import synth
     w = synth.WORKLOADS[WORKLOAD]
     p = synth.make_problem(w)
-    g = oracle.make_geometry(w.N, w.L, w.R, p["theta"], p["delta"][:bins], p["blade_frame"], w.T)
+    g = oracle.make_geometry(w.N, w.L, w.R, p["theta"][:blades], p["delta"], p["blade_frame"][:blades], w.T)
     prm = oracle.ReconParams(lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
-    V = np.zeros((w.T, w.N, w.N, bins), dtype=np.complex128)
-    y = p["y"].astype(np.complex128)
-    return w, g, prm, V, y, w.Nf / bins
+    V = np.zeros((w.T, w.N, w.N, w.Nf), dtype=np.complex128)
+    y = p["y"][:blades].astype(np.complex128)
+    return w, g, prm, V, y, w.B / blades
 
 
-def oracle_steps(n_steps: int, max_seconds: float, bins: int = 8):
+def oracle_steps(n_steps: int, blades: int = SAMPLE_BLADES, max_seconds: float = None):
+    """n_steps oracle iterations on the blade sample.  Each iteration is the
+    oracle's loss and gradient (its data term and adjoint, then its TV terms,
+    exactly as oracle.loss_and_grad composes them) and its Adam step.
+    Returns (steps done, sample seconds, estimated full-workload seconds)."""
     import numpy as np
     import oracle
-    w, g, prm, V, y, scale = oracle_sample(bins)
+    w, g, prm, V, y, scale = oracle_sample(blades)
     m = np.zeros(V.shape + (2,))
     v = np.zeros(V.shape + (2,))
-    done = 0
-    t0 = time.perf_counter()
+    done, t_sample, t_full = 0, 0.0, 0.0
     for k in range(1, n_steps + 1):
-        _, grad = oracle.loss_and_grad(V, y, g, prm)
+        t0 = time.perf_counter()
+        dl, r = oracle.data_loss(V, y, g)           # exact NDFT forward: linear in the samples
+        grad = 2.0 * oracle.adjoint(r, g)           # explicit adjoint: linear in the samples
+        t1 = time.perf_counter()
+        _, gxy = oracle.tv_xy(V, prm.tv_eps)        # whole-volume terms: independent of the samples
+        grad += prm.tv_xy * gxy
+        if prm.tv_t:
+            _, gt = oracle.tv_t(V, prm.tv_eps)
+            grad += prm.tv_t * gt
         V, m, v = oracle.adam_step(V, grad, m, v, k, prm)
+        t2 = time.perf_counter()
         done += 1
-        if time.perf_counter() - t0 > max_seconds:
+        t_sample += t2 - t0
+        t_full += scale * (t1 - t0) + (t2 - t1)
+        if max_seconds is not None and t_sample > max_seconds:
             break
-    dt = time.perf_counter() - t0
-    return done, dt, scale
+    return done, t_sample, t_full
 
 
 def cpu_cores() -> int:
@@ -135,32 +161,61 @@ def cpu_cores() -> int:
     return os.cpu_count() or 1
 
 
+def blas_name() -> str:
+    """The BLAS library numpy's matrix products run on, with its version and threads."""
+    try:
+        from threadpoolctl import threadpool_info
+        for i in threadpool_info():
+            if i.get("user_api") == "blas":
+                return (f"{i.get('internal_api', '?')} {i.get('version', '?')} "
+                        f"({i.get('num_threads', '?')} threads, {os.path.basename(i.get('filepath', ''))})")
+    except Exception:
+        pass
+    try:
+        import numpy as np
+        cfg = np.show_config(mode="dicts")
+        b = cfg.get("Build Dependencies", {}).get("blas", {})
+        return f"{b.get('name', '?')} {b.get('version', '')}".strip()
+    except Exception:
+        return "unknown"
+
+
+def _sample_text(done, t_sample, blades=SAMPLE_BLADES):
+    return (f"{done} FP64 oracle iteration(s) (exact NDFT forward + explicit adjoint, TV, Adam) on "
+            f"{blades} of the 16 blades of the static workload with all 32 bins and the full volume, "
+            f"{t_sample:.1f} s; full-workload time = 16/{blades} x the NDFT time + the measured TV and Adam "
+            f"time (the NDFT costs the same per sample); BLAS {blas_name()}")
+
+
 def cpu_baseline_obj(seconds: float = 20.0) -> dict:
-    done, dt, scale = oracle_steps(1000, seconds)
-    return {"value": done / (dt * scale), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{done} FP64 oracle iteration(s) (exact NDFT forward + explicit adjoint, TV, Adam) "
-                      f"on 8 of the 32 spectral bins of the static workload, {dt:.1f} s; "
-                      f"rate scaled by 8/32 (work is linear in bins)"}
+    done, t_sample, t_full = oracle_steps(1000, max_seconds=seconds)
+    return {"value": done / t_full, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "blas": blas_name(), "sample": _sample_text(done, t_sample)}
 
 
 def run_reference(args):
+    """The oracle arm: W warm-up and K timed oracle iterations on the blade
+    sample (rank 0 only), reported as full-workload iterations/s."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    warm = min(args.warmup, 1)
-    if warm:
-        oracle_steps(warm, 60.0)
-    done, dt, scale = oracle_steps(max(1, args.steps), 120.0)
-    value = done / (dt * scale)
+    if args.warmup:
+        oracle_steps(args.warmup)
+    K = max(1, args.steps)
+    done, t_sample, t_full = oracle_steps(K)
+    value = done / t_full
     import synth
     w = synth.WORKLOADS[WORKLOAD]
+    cfg = workload_config(w)
+    cfg["workload"] += (f" (oracle: each step on {SAMPLE_BLADES} of 16 blades, all bins, full volume; "
+                        f"rate extrapolated to all 16 blades)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": done, "warmup": warm, "ms_per_step": 1000.0 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w),
+            "steps": done, "warmup": args.warmup, "ms_per_step": 1000.0 * t_sample / done,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "ms_per_full_iteration_estimated": 1000.0 * t_full / done,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"{done} oracle iteration(s) on 8 of 32 bins ({dt:.1f} s), "
-                                       f"scaled by 8/32; steps capped to fit 120 s"},
+                             "blas": blas_name(), "sample": _sample_text(done, t_sample)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -356,7 +411,7 @@ def run_ours(args):
     w_rank = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
     prob = synth.make_problem(w_rank)
     plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=local,
-                bin_chunk=args.bin_chunk, row_kernel=args.row_kernel)
+                bin_chunk=args.bin_chunk, row_kernel=args.row_kernel, kb_width=args.kb_width)
     params = ReconParams(iters=1, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
     y = torch.from_numpy(prob["y"]).to(dev)
     Va = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)
@@ -453,13 +508,13 @@ def run_ours(args):
         tr_path = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tr_path):
             with open(tr_path) as f:
-                traffic = json.load(f).get(args.workload, {}).get(dom)
+                traffic = json.load(f).get(f"{args.workload}_w{args.kb_width}", {}).get(dom)
             if traffic is not None:
                 traffic = float(traffic)
         launches = sum(v_[1] for v_ in prof.values())
         from paper_2311_13177_gb300.binding import prop_fp32_fma_peak
         fma = prop_fp32_fma_peak(local)
-        flops = stage_alu_flops(plan)
+        flops = stage_alu_flops(plan, args.kb_width)
         alu = {"fp32_fma_peak_tflops": fma, "peak_source": "measured by prop_fp32_fma_peak",
                "ridge_flop_per_byte": fma * 1e12 / (peak * 1e9)}
         for st_ in ("interp", "spread"):
@@ -473,7 +528,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
-            "config": {**workload_config(w),
+            "config": {**workload_config(w, args.kb_width),
                        "l2": f"inputs larger than L2: each iteration streams a {ws / 1e6:.0f} MB working set "
                              f"(129 MB L2); K iterations back to back in one prop_reconstruct call",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
@@ -505,11 +560,91 @@ def run_ours(args):
             line["serving"] = run_serving(args.serve_requests, args.serve_iters, 7, local)
         if world == 1 and not args.no_projection and args.workload == WORKLOAD:
             line["projection_model"] = run_projection_model(plan, w, prob, dev, peak, K)
+        if world == 1 and args.workload == WORKLOAD and args.kb_width != 6:
+            line["kb_width_6"] = run_width6(w, prob, dev, params, min(K, 2000), local)
+        if world == 1 and not args.no_kplanes and args.workload == WORKLOAD:
+            line["kplanes"] = run_kplanes(dev, peak, local)
         print(json.dumps(line), flush=True)
     plan.destroy()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_width6(w, prob, dev, params, K, device):
+    """The same reconstruction at Kaiser-Bessel width 6 (the configured width;
+    its 3-iteration reconstruction misses the 1e-3 parity bar at this
+    workload, hence not the headline): one prop_reconstruct call of K
+    iterations, CUDA events."""
+    import torch
+    from paper_2311_13177_gb300 import Plan
+    plan = Plan(w.N, w.L, w.R, prob["theta"], prob["delta"], prob["blade_frame"], w.T, device=device, kb_width=6)
+    y = torch.from_numpy(prob["y"]).to(dev)
+    V = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)
+    plan.reconstruct(y, dataclasses.replace(params, iters=20), V, trace=False)
+    torch.cuda.synchronize()
+    V.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.reconstruct(y, dataclasses.replace(params, iters=K), V, trace=False)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.destroy()
+    return {"value": K / (e0.elapsed_time(e1) / 1000.0), "unit": UNIT, "iters": K,
+            "note": "kernel width 6: 36 taps per sample instead of 64; its trajectory drifts 2e-3 to 6e-3 from "
+                    "the exact operator's (bench.py --width-study), above the 1e-3 reconstruction bar"}
+
+
+def run_kplanes(dev, peak, device, iters: int = 20):
+    """One K-Planes iteration (Sec. 4.1 Eq. 3: F = 8 features, two scales) at
+    the dynamic workload's shape: render the volume from the planes, the
+    non-uniform data term and TV with their gradient, the parameter
+    gradients, Adam on the planes.  One prop_kplanes_reconstruct call of
+    `iters` iterations timed with CUDA events, then a profiled call for the
+    stage times.  Algorithmic bytes per iteration: the rendered volume
+    written (|V|), the main path's unfused forward + adjoint + TV gradient
+    (|V| + 4|G| + 3|y| + 3|V|), grad V read by the parameter gradients (|V|):
+    6|V| + 4|G| + 3|y|."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2311_13177_gb300 import Plan, ReconParams
+    w = synth.WORKLOADS["dynamic"]
+    p = synth.make_problem(w)
+    F, S = 8, 2
+    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T, device=device, kb_width=8)
+    count = plan.kplanes_param_count(F, S)
+    rng = np.random.default_rng(5)
+    kp0 = (1.0 + 0.1 * (rng.standard_normal(count) + 1j * rng.standard_normal(count))).astype(np.complex64)
+    y = torch.from_numpy(p["y"]).to(dev)
+    prm = ReconParams(iters=3, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
+    kp = torch.from_numpy(kp0).to(dev)
+    plan.kplanes_reconstruct(y, prm, kp, F, S)  # warm-up (allocates the workspace)
+    kp = torch.from_numpy(kp0).to(dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, tr = plan.kplanes_reconstruct(y, dataclasses.replace(prm, iters=iters), kp, F, S)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    plan.profile_read()
+    plan.profile_enable(True)
+    plan.kplanes_reconstruct(y, dataclasses.replace(prm, iters=iters), torch.from_numpy(kp0).to(dev), F, S)
+    plan.profile_enable(False)
+    prof = {k_: v_ for k_, v_ in plan.profile_read().items() if v_[1] > 0}
+    plan.destroy()
+    V = 8.0 * w.T * w.N * w.N * w.Nf
+    G = 8.0 * w.T * (2 * w.N) ** 2 * w.Nf
+    yb = 8.0 * w.B * w.L * w.R
+    b_iter = 6 * V + 4 * G + 3 * yb
+    return {"value": 1000.0 / ms, "unit": "iters/s", "ms_per_iter": ms, "iters": iters,
+            "config": f"dynamic {w.N}x{w.N}, {w.Nf} bins, {w.T} frames, {w.B} golden-angle blades x {w.L} x {w.R}; "
+                      f"K-Planes F={F}, {S} scales ({count} complex parameters); kernel width 8",
+            "stages_ms_per_iter": {k_: v_[0] / iters for k_, v_ in prof.items()},
+            "roofline": {"bound": "hbm", "algo_bytes_per_iter": b_iter, "achieved_gbs": b_iter / (ms / 1000.0) / 1e9,
+                         "peak": peak, "frac": b_iter / (ms / 1000.0) / 1e9 / peak},
+            "loss_first": float(tr[0]), "loss_last": float(tr[-1])}
 
 
 def run_projection_model(plan, w, prob, dev, peak, K):
@@ -600,9 +735,68 @@ def run_diff_study(args):
                       "rows": rows}), flush=True)
 
 
+def run_width_study(args):
+    """Width-6 against width-8 reconstructions of the same problem over many
+    iterations.  The width-8 NUFFT is two orders of magnitude closer to the
+    exact operator (relative error ~5e-8 against ~8e-6), so its trajectory
+    stands in for the exact one where the FP64 oracle cannot run that long;
+    the relative L2 distance of the two volumes after k iterations is the
+    drift that width 6 adds.  Also times both widths (CUDA events)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2311_13177_gb300 import build as _b
+    _b.build()
+    from paper_2311_13177_gb300 import Plan, ReconParams
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = synth.WORKLOADS[args.workload]
+    p = synth.make_problem(w)
+    y = torch.from_numpy(p["y"]).to(dev)
+    K = args.width_study
+    marks = sorted({m for m in (1, 3, 10, 30, 100, 300, K) if m <= K})
+    out = {}
+    for kbw in (6, 8):
+        plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T, kb_width=kbw)
+        prm = ReconParams(iters=1, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps)
+        a = torch.zeros(plan.vol_shape, dtype=torch.complex64, device=dev)
+        b = torch.empty_like(a)
+        loss = torch.zeros(K, dtype=torch.float64, device=dev)
+        snaps = {}
+        for k in range(1, K + 1):
+            plan.recon_step(y, prm, k, a, b, loss[k - 1:k])
+            a, b = b, a
+            if k in marks:
+                snaps[k] = a.clone()
+        V = torch.zeros_like(a)
+        plan.reconstruct(y, ReconParams(iters=20, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps), V,
+                         trace=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        V.zero_()
+        e0.record()
+        plan.reconstruct(y, ReconParams(iters=K, lr=w.lr, tv_xy=w.tv_xy, tv_t=w.tv_t, tv_eps=w.tv_eps), V,
+                         trace=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[kbw] = (snaps, loss.cpu().numpy(), K / (e0.elapsed_time(e1) / 1000.0))
+        plan.destroy()
+    rows = []
+    for m in marks:
+        v6, v8 = out[6][0][m], out[8][0][m]
+        rows.append({"iters": m, "volume_rel_l2_w6_vs_w8": float(torch.linalg.vector_norm(v6 - v8) /
+                                                                  torch.linalg.vector_norm(v8)),
+                     "loss_rel_w6_vs_w8": float(abs(out[6][1][m - 1] - out[8][1][m - 1]) / abs(out[8][1][m - 1]))})
+    print(json.dumps({"study": "kernel width 6 vs 8 trajectory drift", "workload": workload_config(w)["workload"],
+                      "iters": K, "rows": rows, "iters_per_s": {"6": out[6][2], "8": out[8][2]},
+                      "final_loss": {"6": float(out[6][1][-1]), "8": float(out[8][1][-1])}}), flush=True)
+
+
 def main():
     args = parse()
-    if args.diff_study:
+    if args.width_study:
+        run_width_study(args)
+    elif args.diff_study:
         run_diff_study(args)
     elif args.impl == "reference":
         run_reference(args)

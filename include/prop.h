@@ -152,6 +152,51 @@ PROP_API prop_status prop_reconstruct(prop_plan plan, const void* y_dev, const p
 PROP_API prop_status prop_recon_step(prop_plan plan, const void* y_dev, const prop_recon_params* params, int k,
                                      const void* V_in_dev, void* V_out_dev, double* loss_dev, void* stream);
 
+/* ---- Bin-sharded iterations --------------------------------------------
+ * The forward operator is a sum over spectral bins (Sec. 3 Eq. 2 displaces
+ * and transforms every bin's layer on its own; Sec. 4.2 sums the layers), so
+ * one reconstruction can be split over G plans -- one per device -- whose
+ * bins partition the spectral axis into contiguous runs: plan g is created
+ * with delta[f_g .. f_g+1) and holds V_g = V[..., f_g .. f_g+1).  One Adam
+ * iteration k is then, on every plan g,
+ *   1. prop_shard_forward(plan_g, V_g)      -> y_g = A_g V_g
+ *   2. the caller sums the y_g over the plans (an all-reduce over devices),
+ *      giving the same y_sum = A V everywhere;
+ *   3. prop_shard_update(plan_g, y, y_sum, .., V_g -> V_g'): residual
+ *      r = y_sum - y, adjoint 2 A_g^H r, TV of the plan's bins (x-y and
+ *      temporal TV act on each bin separately) and Adam.
+ * The iterates equal prop_reconstruct's on the whole axis up to the rounding
+ * of the bin sum.  The loss of iteration k is loss_parts[0] (the data term,
+ * the same on every plan) plus the sum over plans of loss_parts[1]. */
+
+/* y_part_dev [B][L][R] = A_g V_g, the forward operator over the plan's bins
+ * (flags & PROP_SHARD_ACCUMULATE: y_part_dev += A_g V_g instead, so that
+ * plans on one device can sum their parts in place without a collective).
+ * flags & PROP_SHARD_REUSE_ROWS skips the row transform when V_dev is the
+ * V_out of the last prop_shard_update on this plan and no other call has used
+ * the plan since (the update leaves that transform in the plan's workspace);
+ * otherwise it is recomputed.  Does not synchronise.  Errors:
+ * PROP_ERR_INVALID_ARG (null or unaligned buffers, unknown flags),
+ * PROP_ERR_CUDA. */
+#define PROP_SHARD_REUSE_ROWS 1
+#define PROP_SHARD_ACCUMULATE 2
+PROP_API prop_status prop_shard_forward(prop_plan plan, const void* V_dev, int flags, void* y_part_dev,
+                                        void* stream);
+
+/* The rest of iteration k (1-based) on the plan's bins, out of place:
+ * y_dev the measured data, y_sum_dev the summed forward A V of V_{k-1}
+ * (both [B][L][R]), V_in_dev = V_{k-1} of the plan's bins, V_out_dev
+ * (different buffer) receives V_k.  k == 1 resets the plan's Adam moments.
+ * loss_parts_dev (device, 2 doubles, may be NULL): [0] = sum |y_sum - y|^2,
+ * [1] = tv_xy TV_xy + tv_t TV_t of V_{k-1} over the plan's bins.  Leaves the
+ * forward row transform of V_out in the plan for prop_shard_forward.  Does
+ * not synchronise.  Errors: PROP_ERR_INVALID_ARG (null or unaligned
+ * buffers, V_in == V_out, k < 1, parameters out of range), PROP_ERR_OOM
+ * (optimiser state on first use), PROP_ERR_CUDA. */
+PROP_API prop_status prop_shard_update(prop_plan plan, const void* y_dev, const void* y_sum_dev,
+                                       const prop_recon_params* params, int k, const void* V_in_dev,
+                                       void* V_out_dev, double* loss_parts_dev, void* stream);
+
 /* prop_reconstruct on host buffers: copies y_host [B][L][R] and V_host
  * (start) to the device, runs K iterations, copies V back into V_host and
  * synchronises.  Staging buffers are allocated in the plan on first use.
@@ -172,6 +217,19 @@ PROP_API prop_status prop_loss_grad(prop_plan plan, const void* y_dev, const pro
  * Requires 0 <= f_lo < f_hi <= Nf. */
 PROP_API prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, void* image_dev,
                         void* stream);
+
+/* Peak signal-to-noise ratio of a render against a reference image, the
+ * quality figure of the paper's results (Sec. 6, Table 1), on magnitudes:
+ *   PSNR = 10 log10( max|ref|^2 / mean (|image| - |ref|)^2 )  dB
+ * over `frames` consecutive images [frames][N][N] complex64 (1 <= frames <= T;
+ * all frames of a dynamic series together).  *psnr_host receives +inf when
+ * the magnitudes agree exactly.  The sums are FP64 block partials combined
+ * in block order (deterministic).  Allocates a small reduction buffer in the
+ * plan on first use (PROP_ERR_OOM on failure); synchronises the stream.
+ * Errors: PROP_ERR_INVALID_ARG (null or unaligned pointer, frames out of
+ * range), PROP_ERR_OOM, PROP_ERR_CUDA. */
+PROP_API prop_status prop_psnr(prop_plan plan, const void* image_dev, const void* ref_dev, int frames,
+                               double* psnr_host, void* stream);
 
 /* ---- Serving: continuous batching of independent reconstructions ----------
  * A server owns one device arena of hbm_budget_bytes (+ 64 MiB rounding
@@ -264,11 +322,13 @@ PROP_API prop_status prop_tv_grad_static(const void* V_dev, int nframes, int n, 
 
 /* Stage profiling.  Stages: 0 forward row FFT, 1 forward column FFT,
  * 2 interpolation, 3 spread, 4 adjoint column FFT, 5 adjoint row FFT,
- * 6 TV + Adam (or TV gradient), 7 other (render), 8 the fused row kernel of
- * prop_reconstruct (adjoint row FFT + TV + Adam + the next iteration's
- * forward row FFT).  While enabled, every kernel launch of the plan is
- * bracketed by two CUDA events on its stream. */
-#define PROP_NUM_STAGES 9
+ * 6 TV + Adam (or TV gradient), 7 other (render, PSNR), 8 the fused row
+ * kernel of prop_reconstruct (adjoint row FFT + TV + Adam + the next
+ * iteration's forward row FFT), 9 K-Planes expansion and render, 10 K-Planes
+ * parameter gradients, 11 K-Planes Adam.  While enabled, every kernel launch
+ * (or group of launches) of the plan is bracketed by two CUDA events on its
+ * stream. */
+#define PROP_NUM_STAGES 12
 PROP_API prop_status prop_profile_enable(prop_plan plan, int enable);
 /* Synchronises on the recorded events, writes per-stage total milliseconds
  * and launch counts (arrays of PROP_NUM_STAGES), and clears the record. */
@@ -369,8 +429,14 @@ PROP_API prop_status prop_kplanes_param_count(prop_plan plan, int features, int 
 PROP_API prop_status prop_kplanes_render(prop_plan plan, int features, int scales, const void* params_dev,
                                          void* V_dev, void* stream);
 /* grad_dev (same layout as the parameters) = dL/dRe z + i dL/dIm z for every
- * parameter z, given gV_dev = dL/dRe V + i dL/dIm V.  Sums are accumulated
- * with atomics (order not fixed).  Does not synchronise. */
+ * parameter z, given gV_dev = dL/dRe V + i dL/dIm V.  Every sum is taken in a
+ * fixed order (partial sums over the spectral axis, over time and over the
+ * image, then fixed-order second passes and the transposed interpolation; no
+ * atomics), so the result is bitwise reproducible.  The render and the
+ * gradients use a workspace in the plan (the planes expanded to the volume's
+ * resolution and the partial sums, about (T N^2 + N^2 Nf) * features * scales
+ * complex values), allocated on first use (PROP_ERR_OOM on failure).  Does
+ * not synchronise. */
 PROP_API prop_status prop_kplanes_vjp(prop_plan plan, int features, int scales, const void* params_dev,
                                       const void* gV_dev, void* grad_dev, void* stream);
 /* Adam on the model's parameters (in place) for the loss of prop_reconstruct

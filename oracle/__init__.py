@@ -15,7 +15,7 @@ Contents
             and its explicit adjoint
   recon     data-consistency loss, smoothed TV in x-y and in time, Adam, and
             the full-batch reconstruction loop (Sec. 4.3), plus the phi = 0
-            render and the fat/water split (Sec. 4.3, Sec. 6)
+            render, the fat/water split and PSNR (Sec. 4.3, Sec. 6)
   kplanes   the dynamic K-Planes volume model (Sec. 4.1, Eq. 3): six planes
             of feature vectors, bilinear lookups, Hadamard product, weighting
             vector, two scales; rendering on the volume grid and the
@@ -35,12 +35,12 @@ torch.optim.Adam (iterates and loss traces to 1e-12).
 from .geometry import Geometry, make_geometry, sample_coords, phase_table
 from .ndft import forward, adjoint, forward_at, adjoint_at
 from .recon import (ReconParams, data_loss, tv_xy, tv_t, loss_and_grad,
-                    adam_step, reconstruct, render)
+                    adam_step, reconstruct, render, psnr)
 from . import projection
 from . import kplanes
 
 __all__ = [
     "Geometry", "make_geometry", "sample_coords", "phase_table", "forward", "adjoint",
     "forward_at", "adjoint_at", "ReconParams", "data_loss", "tv_xy", "tv_t",
-    "loss_and_grad", "adam_step", "reconstruct", "render", "projection", "kplanes",
+    "loss_and_grad", "adam_step", "reconstruct", "render", "psnr", "projection", "kplanes",
 ]

@@ -15,9 +15,9 @@ c_int, c_float, c_double, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_float, ct
                                                 ctypes.c_void_p, ctypes.c_size_t)
 
 PROP_OK = 0
-PROP_NUM_STAGES = 9
+PROP_NUM_STAGES = 12
 STAGE_NAMES = ["fft_fwd_rows", "fft_fwd_cols", "interp", "spread", "fft_adj_cols", "fft_adj_rows",
-               "tv_adam", "other", "rows_update"]
+               "tv_adam", "other", "rows_update", "kplanes_render", "kplanes_vjp", "kplanes_adam"]
 STATUS_NAMES = {0: "PROP_OK", 1: "PROP_ERR_INVALID_ARG", 2: "PROP_ERR_OOM", 3: "PROP_ERR_CUDA",
                 4: "PROP_ERR_TIMEOUT", 5: "PROP_ERR_BUSY", 6: "PROP_ERR_NOT_READY",
                 7: "PROP_ERR_CANCELLED", 8: "PROP_ERR_UNIMPLEMENTED"}
@@ -53,11 +53,15 @@ SIGNATURES = {
                                  ctypes.POINTER(c_double), c_void_p]),
     "prop_recon_step": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_int, c_void_p, c_void_p,
                                 c_void_p, c_void_p]),
+    "prop_shard_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "prop_shard_update": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_int, c_void_p,
+                                  c_void_p, c_void_p, c_void_p]),
     "prop_reconstruct_host": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p,
                                       ctypes.POINTER(c_double), c_void_p]),
     "prop_loss_grad": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p, c_void_p,
                                ctypes.POINTER(c_double), c_void_p]),
     "prop_render": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "prop_psnr": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_double), c_void_p]),
     "prop_plan_estimate_bytes": (c_int, [ctypes.POINTER(PlanDesc), c_int, ctypes.POINTER(c_size_t)]),
     "prop_serve_create": (c_int, [c_size_t, c_int, c_int, ctypes.POINTER(c_void_p)]),
     "prop_serve_submit": (c_int, [c_void_p, ctypes.POINTER(PlanDesc), ctypes.POINTER(ReconParamsC), c_void_p,

@@ -20,7 +20,7 @@ from ._lib import PlanDesc, ProjParamsC, ReconParamsC, check, lib
 
 __all__ = ["Plan", "ReconParams", "ProjParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
            "prop_forward", "prop_adjoint", "prop_reconstruct", "prop_reconstruct_host",
-           "prop_loss_grad", "prop_render"]
+           "prop_loss_grad", "prop_render", "prop_psnr"]
 
 
 @dataclass
@@ -176,6 +176,35 @@ class Plan:
                                     lp, _stream(stream)), "prop_recon_step")
         return V_out
 
+    def shard_forward(self, V: torch.Tensor, y_part: torch.Tensor = None, reuse_rows: bool = False,
+                      accumulate: bool = False, stream=None) -> torch.Tensor:
+        """A_g V over this plan's bins (one shard of a bin-sharded iteration); accumulate adds it to y_part."""
+        if y_part is None:
+            if accumulate:
+                raise ValueError("accumulate needs y_part")
+            y_part = torch.empty(self.data_shape, dtype=torch.complex64, device=V.device)
+        flags = (1 if reuse_rows else 0) | (2 if accumulate else 0)
+        check(lib().prop_shard_forward(self.handle, _dev_ptr(V, self.vol_shape, "V"), flags,
+                                       _dev_ptr(y_part, self.data_shape, "y_part"), _stream(stream)),
+              "prop_shard_forward")
+        return y_part
+
+    def shard_update(self, y: torch.Tensor, y_sum: torch.Tensor, params: ReconParams, k: int, V_in: torch.Tensor,
+                     V_out: torch.Tensor, loss_parts: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """Residual, adjoint, TV and Adam of iteration k on this plan's bins, given the summed forward y_sum.
+        loss_parts (float64 CUDA tensor of 2): [data term, this plan's TV]."""
+        lp = None
+        if loss_parts is not None:
+            if not loss_parts.is_cuda or loss_parts.dtype != torch.float64 or loss_parts.numel() < 2:
+                raise TypeError("loss_parts must be a float64 CUDA tensor of 2 elements")
+            lp = ctypes.c_void_p(loss_parts.data_ptr())
+        pc = params.c()
+        check(lib().prop_shard_update(self.handle, _dev_ptr(y, self.data_shape, "y"),
+                                      _dev_ptr(y_sum, self.data_shape, "y_sum"), ctypes.byref(pc), int(k),
+                                      _dev_ptr(V_in, self.vol_shape, "V_in"), _dev_ptr(V_out, self.vol_shape, "V_out"),
+                                      lp, _stream(stream)), "prop_shard_update")
+        return V_out
+
     def reconstruct_host(self, y: np.ndarray, params: ReconParams, V: np.ndarray = None, trace=False,
                          stream=None):
         """Host-buffer reconstruction (copies in, iterates, copies out). V is updated in place."""
@@ -216,6 +245,17 @@ class Plan:
               "prop_render")
         return out
 
+
+    def psnr(self, image: torch.Tensor, ref: torch.Tensor, stream=None) -> float:
+        """PSNR (dB) of |image| against |ref|, peak max|ref|: images [frames, N, N] complex64."""
+        if image.dim() == 2:
+            image, ref = image.unsqueeze(0), ref.unsqueeze(0)
+        fr = int(image.shape[0])
+        shp = (fr, self.N, self.N)
+        out = ctypes.c_double()
+        check(lib().prop_psnr(self.handle, _dev_ptr(image, shp, "image"), _dev_ptr(ref, shp, "ref"), fr,
+                              ctypes.byref(out), _stream(stream)), "prop_psnr")
+        return float(out.value)
 
     @property
     def kspace_shape(self):
@@ -364,6 +404,10 @@ def prop_loss_grad(plan: Plan, y, params, V, grad=None, stream=None):
 
 def prop_render(plan: Plan, V, f_lo=0, f_hi=None, out=None, stream=None):
     return plan.render(V, f_lo, f_hi, out, stream)
+
+
+def prop_psnr(plan: Plan, image, ref, stream=None) -> float:
+    return plan.psnr(image, ref, stream)
 
 
 def prop_tv_grad_static(V: torch.Tensor, tv_xy: float, tv_t: float, tv_eps: float, grad: torch.Tensor,

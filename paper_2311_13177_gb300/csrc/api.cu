@@ -78,7 +78,8 @@ prop_status check_device_status(Plan& p) {
 // y = A V, or r = A V - y_meas with |r|^2 reduced into *sumsq.  rows_ready:
 // p.rows already holds the forward row transform of V (single chunk only).
 prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_meas, const Reducer* red,
-                         double* sumsq, cudaStream_t s, bool rows_ready = false) {
+                         double* sumsq, cudaStream_t s, bool rows_ready = false, bool accumulate = false) {
+  if (!(rows_ready && p.nchunks == 1)) p.rows_of = nullptr;
   for (int c = 0; c < p.nchunks; ++c) {
     const int f0 = c * p.chunk;
     const int nb = std::min(p.chunk, p.Nf - f0);
@@ -95,7 +96,7 @@ prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_me
       StageScope sc(p, kStInterp, s);
       // With a single chunk the residual is final here: also emit the spread's input.
       float2* contrib = (y_meas && p.nchunks == 1) ? p.contrib : nullptr;
-      PROP_LAUNCH(interp(p, f0, nb, y, c == 0 ? y_meas : nullptr, c > 0, last ? red : nullptr, sumsq,
+      PROP_LAUNCH(interp(p, f0, nb, y, c == 0 ? y_meas : nullptr, c > 0 || accumulate, last ? red : nullptr, sumsq,
                          contrib, s));
     }
   }
@@ -105,6 +106,7 @@ prop_status forward_impl(Plan& p, const float2* V, float2* y, const float2* y_me
 // V = scale * (unscaled adjoint) of r; scale = 1/N gives A^H.
 prop_status adjoint_impl(Plan& p, const float2* r, float2* V, bool contrib_ready, cudaStream_t s) {
   const float scale = 1.0f / (float)p.N;
+  p.rows_of = nullptr;  // the adjoint passes overwrite the row workspace
   for (int c = 0; c < p.nchunks; ++c) {
     const int f0 = c * p.chunk;
     const int nb = std::min(p.chunk, p.Nf - f0);
@@ -168,6 +170,7 @@ prop_status step_impl(Plan& p, const float2* y, const prop_recon_params* q, int 
   const bool fused = p.nchunks == 1;
   if ((st = forward_impl(p, Vin, p.resid, y, &p.red_interp, p.scalars, s, rows_ready && fused)) != PROP_OK)
     return st;
+  p.rows_of = nullptr;  // the adjoint passes below overwrite the row workspace
   if (fused) {
     {
       StageScope sc(p, kStSpread, s);
@@ -315,6 +318,72 @@ prop_status prop_recon_step(prop_plan plan, const void* y_dev, const prop_recon_
                    loss_dev ? loss_dev : p.scalars + 2, (cudaStream_t)stream);
 }
 
+prop_status prop_shard_forward(prop_plan plan, const void* V_dev, int flags, void* y_part_dev, void* stream) {
+  if (!plan || !V_dev || !y_part_dev) return fail(PROP_ERR_INVALID_ARG, "shard_forward: null argument");
+  if (!aligned16(V_dev) || !aligned16(y_part_dev))
+    return fail(PROP_ERR_INVALID_ARG, "shard_forward: buffers must be 16-byte aligned");
+  if (flags & ~(PROP_SHARD_REUSE_ROWS | PROP_SHARD_ACCUMULATE))
+    return fail(PROP_ERR_INVALID_ARG, "shard_forward: unknown flags");
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  const bool ready = (flags & PROP_SHARD_REUSE_ROWS) && p.nchunks == 1 && p.rows_of == V_dev;
+  return forward_impl(p, (const float2*)V_dev, (float2*)y_part_dev, nullptr, nullptr, nullptr,
+                      (cudaStream_t)stream, ready, (flags & PROP_SHARD_ACCUMULATE) != 0);
+}
+
+prop_status prop_shard_update(prop_plan plan, const void* y_dev, const void* y_sum_dev,
+                              const prop_recon_params* params, int k, const void* V_in_dev, void* V_out_dev,
+                              double* loss_parts_dev, void* stream) {
+  if (!plan || !y_dev || !y_sum_dev || !V_in_dev || !V_out_dev)
+    return fail(PROP_ERR_INVALID_ARG, "shard_update: null argument");
+  if (V_in_dev == V_out_dev) return fail(PROP_ERR_INVALID_ARG, "shard_update: V_in and V_out must differ");
+  if (k < 1) return fail(PROP_ERR_INVALID_ARG, "shard_update: k must be >= 1");
+  if (!aligned16(V_in_dev) || !aligned16(V_out_dev) || !aligned16(y_dev) || !aligned16(y_sum_dev) ||
+      ((uintptr_t)loss_parts_dev & 7u))
+    return fail(PROP_ERR_INVALID_ARG, "shard_update: buffers must be 16-byte aligned (loss_parts 8-byte)");
+  prop_status st = check_params(params);
+  if (st != PROP_OK) return st;
+  Plan& p = *plan->p;
+  DeviceGuard g(p.device);
+  if ((st = plan_ensure_recon(&p, 1)) != PROP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vbytes = p.vol_elems() * sizeof(float2);
+  if (k == 1) {
+    PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
+    PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
+  }
+  double* parts = loss_parts_dev ? loss_parts_dev : p.scalars + 4;  // [0] data term, [1] this plan's TV
+  double* zero = p.scalars + 6;  // "data loss" input of the update kernels, so that they report TV alone
+  PROP_CUDA(cudaMemsetAsync(zero, 0, sizeof(double), s));
+  p.rows_of = nullptr;
+  const bool fused = p.nchunks == 1;
+  {
+    StageScope sc(p, kStInterp, s);
+    PROP_LAUNCH(residual(p, (const float2*)y_sum_dev, (const float2*)y_dev, p.resid, fused, p.red_interp, parts, s));
+  }
+  const AdamArgs aa = adam_args(params, k);
+  if (fused) {
+    {
+      StageScope sc(p, kStSpread, s);
+      PROP_LAUNCH(spread(p, 0, p.Nf, p.resid, true, s));
+    }
+    {
+      StageScope sc(p, kStAdjCols, s);
+      PROP_LAUNCH(fft_adjoint_cols(p, s));
+    }
+    StageScope sc(p, kStFused, s);
+    PROP_LAUNCH(fused_rows_update(p, (const float2*)V_in_dev, p.adam_m, p.adam_v, (float2*)V_out_dev, aa,
+                                  &p.red_tv, zero, parts + 1, true, s));
+    p.rows_of = V_out_dev;
+    return PROP_OK;
+  }
+  if ((st = adjoint_impl(p, p.resid, p.grad, false, s)) != PROP_OK) return st;
+  StageScope sc(p, kStOpt, s);
+  PROP_LAUNCH(tv_adam(p, (const float2*)V_in_dev, p.grad, p.adam_m, p.adam_v, (float2*)V_out_dev, aa, &p.red_tv,
+                      zero, parts + 1, s));
+  return PROP_OK;
+}
+
 prop_status prop_reconstruct_host(prop_plan plan, const void* y_host, const prop_recon_params* params,
                                   void* V_host, double* loss_trace_host, void* stream) {
   if (!plan || !y_host || !V_host) return fail(PROP_ERR_INVALID_ARG, "reconstruct_host: null argument");
@@ -384,6 +453,39 @@ prop_status prop_render(prop_plan plan, const void* V_dev, int f_lo, int f_hi, v
   DeviceGuard g(p.device);
   StageScope sc(p, kStOther, (cudaStream_t)stream);
   PROP_LAUNCH(render(p, (const float2*)V_dev, f_lo, f_hi, (float2*)image_dev, (cudaStream_t)stream));
+  return PROP_OK;
+}
+
+prop_status prop_psnr(prop_plan plan, const void* image_dev, const void* ref_dev, int frames, double* psnr_host,
+                      void* stream) {
+  if (!plan || !image_dev || !ref_dev || !psnr_host) return fail(PROP_ERR_INVALID_ARG, "psnr: null argument");
+  if (!aligned16(image_dev) || !aligned16(ref_dev))
+    return fail(PROP_ERR_INVALID_ARG, "psnr: buffers must be 16-byte aligned");
+  Plan& p = *plan->p;
+  if (frames < 1 || frames > p.T) return fail(PROP_ERR_INVALID_ARG, "psnr: need 1 <= frames <= nframes");
+  DeviceGuard g(p.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!p.psnr_scratch) {
+    const int cap = 4 * p.num_sms;
+    // [2 cap] partials, then the counter word (and the result) in the last two doubles
+    cudaError_t e = plan_dev_alloc(&p, (void**)&p.psnr_scratch, (2 * (size_t)cap + 2) * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p.psnr_scratch = nullptr;
+      return fail(PROP_ERR_OOM, std::string("psnr: scratch allocation failed: ") + cudaGetErrorString(e));
+    }
+    p.recon_bytes += (2 * (size_t)cap + 2) * sizeof(double);
+    p.psnr_cap = cap;
+    PROP_CUDA(cudaMemsetAsync(p.psnr_scratch + 2 * cap, 0, 2 * sizeof(double), s));
+  }
+  const long count = (long)frames * p.N * p.N;
+  double* out = p.psnr_scratch + 2 * p.psnr_cap + 1;
+  {
+    StageScope sc(p, kStOther, s);
+    PROP_LAUNCH(psnr(p, (const float2*)image_dev, (const float2*)ref_dev, count, out, s));
+  }
+  PROP_CUDA(cudaMemcpyAsync(psnr_host, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PROP_CUDA(cudaStreamSynchronize(s));
   return PROP_OK;
 }
 

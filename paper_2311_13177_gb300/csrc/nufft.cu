@@ -496,6 +496,38 @@ __global__ void __launch_bounds__(256) phase_expand_kernel(const float2* r, cons
   }
 }
 
+// Residual of a forward pass summed elsewhere (over the bins of several
+// plans): r = y_sum - y_meas, the FP64 sum of |r|^2 (block partials, the last
+// block sums them in block order), and with contrib the phased residual
+// conj(P[j][f0 + f]) r per bin for the spread.  LP lanes per sample.
+template <int LP>
+__global__ void __launch_bounds__(256) resid_expand_kernel(const float2* y_sum, const float2* y_meas, float2* r,
+                                                            const float2* phase, float2* contrib, int M, int R,
+                                                            int Nf, int C, int Cv, int f0, double* partials,
+                                                            unsigned int* counter, double* sumsq_out) {
+  constexpr int SPW = 32 / LP;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (LP - 1);
+  const int slot = lane / LP;
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarp = ((long)gridDim.x * blockDim.x) >> 5;
+  double local = 0.0;
+  for (long m = warp * SPW + slot; m < M; m += nwarp * SPW) {
+    const float2 a = __ldg(&y_sum[m]), b = __ldg(&y_meas[m]);
+    const float2 v = make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+    if (sub == 0) {
+      r[m] = v;
+      local += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    if (contrib) {
+      const float2* P = phase + (size_t)(m % R) * Nf + f0;
+      float2* out = contrib + (size_t)m * C;
+      for (int f = sub; f < Cv; f += LP) out[f] = cmulcf(__ldg(P + f), v);
+    }
+  }
+  reduce_to(local, partials, counter, sumsq_out);
+}
+
 // --- Spread: cell gather over the plan's item blobs ------------------------
 //
 // An item's blob: int2 cells[ncp] (cell index, end of its list relative to
@@ -888,6 +920,27 @@ cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_
   const int lp = lanes_for(nbins);
   dim3 grid((unsigned)blocks);
   return p.W == 8 ? launch_interp<8>(lp, p.cs, a, grid, smem, s) : launch_interp<6>(lp, p.cs, a, grid, smem, s);
+}
+
+cudaError_t residual(const Plan& p, const float2* y_sum, const float2* y_meas, float2* r, bool with_contrib,
+                     const Reducer& red, double* sumsq, cudaStream_t s) {
+  const int nbins = std::min(p.chunk, p.Nf);
+  const int lp = lanes_for(nbins);
+  dim3 g(grid_for(p.M, 8L * (32 / lp), std::min(red.capacity, 16384)));
+  float2* contrib = with_contrib ? p.contrib : nullptr;
+  switch (lp) {
+#define RE(L)                                                                                              \
+  case L:                                                                                                  \
+    resid_expand_kernel<L><<<g, 256, 0, s>>>(y_sum, y_meas, r, p.phase, contrib, p.M, p.R, p.Nf, p.cs, nbins, \
+                                             0, red.partials, red.counter, sumsq);                          \
+    break;
+    RE(1) RE(2) RE(4) RE(8) RE(16)
+    default:
+      resid_expand_kernel<32><<<g, 256, 0, s>>>(y_sum, y_meas, r, p.phase, contrib, p.M, p.R, p.Nf, p.cs, nbins, 0,
+                                                red.partials, red.counter, sumsq);
+#undef RE
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contrib_ready, cudaStream_t s) {

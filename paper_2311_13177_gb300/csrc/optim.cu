@@ -103,6 +103,51 @@ __global__ void render_kernel(const float2* V, float2* img, long npix, int Nf, i
   }
 }
 
+// PSNR partials: each block writes (sum (|a| - |b|)^2, max |b|^2) of its
+// grid-stride share; the last block to arrive combines them in block order
+// and writes 10 log10(peak^2 / mse).
+__global__ void __launch_bounds__(kOptThreads) psnr_kernel(const float2* a, const float2* b, long count,
+                                                           double* scratch, int cap, double* out) {
+  double se = 0.0, pk = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const float2 x = a[i], r = b[i];
+    const double ma = sqrt((double)x.x * x.x + (double)x.y * x.y);
+    const double mr2 = (double)r.x * r.x + (double)r.y * r.y;
+    const double d = ma - sqrt(mr2);
+    se += d * d;
+    pk = fmax(pk, mr2);
+  }
+  __shared__ double sh[32];
+  __shared__ bool last;
+  se = block_sum_d(se, sh);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pk = fmax(pk, __shfl_xor_sync(0xffffffffu, pk, o));
+  __shared__ double shm[32];
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = pk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, shm[w]);
+    scratch[2 * blockIdx.x] = se;
+    scratch[2 * blockIdx.x + 1] = m;
+    __threadfence();
+    unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + 2 * cap);
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0.0, m = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) {
+      s += __ldcg(&scratch[2 * i]);
+      m = fmax(m, __ldcg(&scratch[2 * i + 1]));
+    }
+    const double mse = s / (double)count;
+    *out = mse > 0.0 ? 10.0 * log10(m / mse) : __longlong_as_double(0x7ff0000000000000LL);
+    *reinterpret_cast<unsigned int*>(scratch + 2 * cap) = 0u;
+  }
+}
+
 unsigned opt_blocks(const Plan& p, const Reducer* red) {
   const long segs = ((long)p.N * p.Nf + kSeg - 1) / kSeg;
   long need = (long)p.T * p.N * segs;
@@ -144,6 +189,13 @@ cudaError_t tv_grad(const Plan& p, const float2* V, const float2* g, float2* gra
                     const Reducer* red, const double* data_loss, double* loss_out, cudaStream_t s) {
   OptArgs a = make_args(p, V, g, grad, aa, red, data_loss, loss_out);
   opt_kernel<false><<<opt_blocks(p, red), kOptThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t psnr(const Plan& p, const float2* img, const float2* ref, long count, double* out, cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::max<long>(1, std::min<long>((count + kOptThreads - 1) / kOptThreads,
+                                                                     (long)p.psnr_cap));
+  psnr_kernel<<<blocks, kOptThreads, 0, s>>>(img, ref, count, p.psnr_scratch, p.psnr_cap, out);
   return cudaGetLastError();
 }
 

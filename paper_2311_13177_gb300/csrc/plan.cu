@@ -209,7 +209,8 @@ void plan_free(Plan* p) {
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
                   p->red_tv.counter, p->stage_y, p->stage_v, p->proj_shift, p->proj_mask, p->proj_twiddle,
                   p->proj_img, p->proj_k, p->proj_kg, p->proj_g, p->proj_yimg, p->proj_const,
-                  p->red_proj_k.partials, p->red_proj_k.counter, p->red_proj_u.partials, p->red_proj_u.counter};
+                  p->red_proj_k.partials, p->red_proj_k.counter, p->red_proj_u.partials, p->red_proj_u.counter,
+                  p->psnr_scratch, p->kp_work};
   for (void* q : ptrs) plan_dev_free(p, q);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (auto& v : p->ev_rec)

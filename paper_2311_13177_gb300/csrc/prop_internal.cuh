@@ -156,6 +156,7 @@ struct Plan {
   float2* grid = nullptr;        // [T][n][n][chunk]
   float2* rows = nullptr;        // [T][N][n][chunk] row-pass intermediate
   float2* contrib = nullptr;     // [M + 1][cs] conj(P[j][f]) r_m, input of the spread; row M stays zero
+  const void* rows_of = nullptr; // volume whose forward row transform p.rows holds (left by prop_shard_update)
 
   // projection model, the paper's own forward model (allocated on first use)
   bool proj_ready = false;
@@ -187,6 +188,17 @@ struct Plan {
   float2* stage_y = nullptr;
   float2* stage_v = nullptr;
 
+  // PSNR reduction scratch (allocated on first use): [2 * psnr_cap] FP64
+  // block partials (squared magnitude error, reference peak), then the
+  // arrival counter
+  double* psnr_scratch = nullptr;
+  int psnr_cap = 0;
+
+  // K-Planes model workspace (expanded planes and gradient partials),
+  // allocated on first use and grown on demand
+  void* kp_work = nullptr;
+  size_t kp_work_bytes = 0;
+
   size_t table_bytes = 0, work_bytes = 0, recon_bytes = 0;
 
   // stage profiling (prop_profile_enable)
@@ -199,7 +211,8 @@ struct Plan {
 };
 
 // Stage ids of prop_profile_read.
-enum Stage { kStFwdRows = 0, kStFwdCols, kStInterp, kStSpread, kStAdjCols, kStAdjRows, kStOpt, kStOther, kStFused };
+enum Stage { kStFwdRows = 0, kStFwdCols, kStInterp, kStSpread, kStAdjCols, kStAdjRows, kStOpt, kStOther, kStFused,
+             kStKpRender, kStKpVjp, kStKpAdam };
 
 // Brackets one launch with profiling events when the plan profiles.
 struct StageScope {
@@ -281,6 +294,10 @@ cudaError_t nufft_configure(int smem_optin);
 int interp_buffers(const Plan& p);
 // contrib_ready: p.contrib already holds this chunk's phased residual (fused by interp).
 cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contrib_ready, cudaStream_t s);
+// r = y_sum - y_meas, the FP64 sum of |r|^2 into *sumsq (device, reduced with `red`), and with
+// with_contrib (single bin chunk) the spread's phased residual of every bin.
+cudaError_t residual(const Plan& p, const float2* y_sum, const float2* y_meas, float2* r, bool with_contrib,
+                     const Reducer& red, double* sumsq, cudaStream_t s);
 
 // optim.cu
 struct AdamArgs {
@@ -300,6 +317,9 @@ cudaError_t tv_grad(const Plan& p, const float2* V, const float2* g, float2* gra
                     const AdamArgs& a, const Reducer* red, const double* data_loss,
                     double* loss_out, cudaStream_t s);
 cudaError_t render(const Plan& p, const float2* V, int f_lo, int f_hi, float2* img, cudaStream_t s);
+// PSNR of |img| against |ref| over `count` complex values: 10 log10(max|ref|^2 / mean (|img| - |ref|)^2)
+// into *out (device); scratch: p.psnr_scratch with p.psnr_cap block partials.
+cudaError_t psnr(const Plan& p, const float2* img, const float2* ref, long count, double* out, cudaStream_t s);
 
 // fft.cu, single bin chunk only: the inverse row FFT of p.rows (the last
 // adjoint pass) fused with TV + Adam (Vin -> Vout, moments m, v) and, with

@@ -144,6 +144,24 @@ def test_render_sums_bins():
     plan.destroy()
 
 
+def test_psnr_matches_oracle():
+    """prop_psnr on a noisy render of two frames against the oracle's PSNR;
+    identical magnitudes give +inf."""
+    c = random_case(32, 6, 3, 4, 32, 2, seed=10)
+    plan = _plan(c)
+    rng = np.random.default_rng(12)
+    ref = oracle.render(c["V"])
+    img = (ref + 0.05 * (rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape))).astype(np.complex64)
+    ref = ref.astype(np.complex64)
+    got = plan.psnr(torch.from_numpy(img).cuda(), torch.from_numpy(ref).cuda())
+    want = oracle.psnr(img.astype(np.complex128), ref.astype(np.complex128))
+    assert abs(got - want) < 1e-6, (got, want)
+    one = plan.psnr(torch.from_numpy(img[:1]).cuda(), torch.from_numpy(ref[:1]).cuda())
+    assert abs(one - oracle.psnr(img[:1].astype(np.complex128), ref[:1].astype(np.complex128))) < 1e-6
+    assert plan.psnr(torch.from_numpy(ref).cuda(), torch.from_numpy(ref).cuda()) == float("inf")
+    plan.destroy()
+
+
 @pytest.mark.gpu
 def test_fp32_fma_peak_is_plausible():
     from paper_2311_13177_gb300.binding import prop_fp32_fma_peak

@@ -45,6 +45,40 @@ def test_reconstruction_matches_oracle(name, iters, kbw):
     assert tro[-1] < tro[0]
 
 
+@pytest.mark.parametrize("kbw", [8])
+def test_full_static_workload_three_iterations_match_oracle(kbw):
+    """The benchmark's own configuration (256^2, 32 bins, 16 blades x 24 x
+    256, kernel width 8 as benchmarked): 3 iterations of prop_reconstruct
+    against the FP64 oracle's exact-NDFT iterations (about 20 s each on the
+    host cores).  Width 6 misses this bar here (3.3e-3 after 3 iterations):
+    Adam's first step is the sign of each gradient component, and the
+    width-6 operator error (~8e-6) flips the components whose gradient is
+    that close to zero."""
+    from paper_2311_13177_gb300 import Plan
+    w, p = workload_case("static")
+    g = geometry(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+    pg, po = _params(w, 3)
+    plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T, kb_width=kbw)
+    V, tr = plan.reconstruct(torch.from_numpy(p["y"]).cuda(), pg)
+    V = V.cpu().numpy()
+    plan.destroy()
+    Vo, tro = _oracle_static_3iters(p, g, po)
+    e = rel(V, Vo)
+    et = np.max(np.abs(tr - tro) / np.abs(tro))
+    print(f"width {kbw}: volume rel {e:.3e}, trace rel {et:.3e}")
+    assert e < TOL_RECON, e
+    assert et < 1e-4, et
+
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_static_3iters(p, g, po):
+    if "static3" not in _ORACLE_CACHE:
+        _ORACLE_CACHE["static3"] = oracle.reconstruct(p["y"].astype(np.complex128), g, po)
+    return _ORACLE_CACHE["static3"]
+
+
 def test_multi_chunk_reconstruction_matches_oracle():
     """Bins in two grid passes (chunk 4 of 8): the separate adjoint-row and
     TV + Adam kernels instead of the fused row kernel."""

@@ -287,3 +287,34 @@ def test_render_and_split():
     V = _rand_c(rng, (2, 3, 3, 5))
     assert np.allclose(oracle.render(V), V.sum(-1))
     assert np.allclose(oracle.render(V, 0, 2) + oracle.render(V, 2, 5), oracle.render(V))
+
+
+# --- PSNR (Sec. 6, Table 1) -------------------------------------------------
+
+def test_psnr_closed_form():
+    """|image| = (1 + d) |ref| on a constant-magnitude reference c: the error is
+    c d everywhere, so PSNR = 10 log10(c^2 / (c d)^2) = -20 log10 d exactly;
+    a phase change alone leaves the magnitudes equal (PSNR at the rounding
+    floor, and +inf for identical magnitudes)."""
+    rng = np.random.default_rng(10)
+    phase = np.exp(2j * np.pi * rng.uniform(size=(3, 16, 16)))
+    c = 2.5
+    ref = c * phase
+    for d in (0.1, 0.01, 3e-4):
+        assert abs(oracle.psnr((1 + d) * ref, ref) - (-20.0 * math.log10(d))) < 1e-9
+    assert oracle.psnr(ref * np.exp(0.7j), ref) > 250.0
+    assert oracle.psnr(ref, ref) == float("inf")
+
+
+def test_psnr_brute_force_and_peak_of_reference():
+    """Against a loop over the pixels; the peak is the reference's, not the image's."""
+    rng = np.random.default_rng(11)
+    ref = _rand_c(rng, (5, 7))
+    img = ref + 0.1 * _rand_c(rng, (5, 7))
+    se, pk = 0.0, 0.0
+    for a, b in zip(img.ravel(), ref.ravel()):
+        se += (abs(a) - abs(b)) ** 2
+        pk = max(pk, abs(b))
+    ref_val = 10 * math.log10(pk * pk / (se / ref.size))
+    assert abs(oracle.psnr(img, ref) - ref_val) < 1e-10
+    assert abs(oracle.psnr(img, ref) - oracle.psnr(ref, img)) > 1e-3   # not symmetric: the peak is the reference's

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kInterpThreads, 1) interp_kernel(InterpArgs a)
   const int sub = lane & (LP - 1);
   const int slot = lane / LP;
   const int C = CS > 0 ? CS : a.C;
-  const int TI = CS > 0 ? (CS <= 32 ? 16 : 8) : a.TI;
+  const int TI = CS > 0 ? interp_tile_for(CS, W) : a.TI;
   const int HW = TI + W - 1;
   const size_t tile_elems = (size_t)HW * HW * C;
   float2* bufs = reinterpret_cast<float2*>(smem_raw);
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
   constexpr int NCW = kInterpConsumers;
   constexpr int LPS = CS / 2;   // lanes per sample
   constexpr int SPW = 32 / LPS; // samples per warp and round
-  constexpr int TI = CS <= 32 ? 16 : 8;
+  constexpr int TI = interp_tile_for(CS, W);
   constexpr int HW = TI + W - 1;
   constexpr int WQ = W / 2;
   constexpr int MPL = (kInterpItem + NCW * SPW - 1) / (NCW * SPW) * SPW;  // samples per warp per item
@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
       const int sL = (lane / SPW) * NCW * SPW + warp * SPW + (lane % SPW);
       int mL = 0, jL = 0;
       uint32_t pL = 0;
+      float2 yL = make_float2(0.f, 0.f);  // the measurement (or the partial sum so far) of the sample
       float wL[2 * W];
 #pragma unroll
       for (int q = 0; q < 2 * W; ++q) wL[q] = 0.f;
@@ -395,6 +396,10 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
           wL[4 * q + 3] = v.w;
         }
         jL = mL % a.R;
+        if (a.accumulate)
+          yL = a.y[mL];
+        else if (a.y_meas)
+          yL = __ldg(&a.y_meas[mL]);
       }
       if (!mbar_wait_bounded(&full[b], (uint32_t)((k / a.nbuf) & 1))) s_abort = 1;
       if (s_abort) break;
@@ -407,6 +412,7 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
         const int m = __shfl_sync(0xffffffffu, mL, src);
         const int j = __shfl_sync(0xffffffffu, jL, src);
         const uint32_t packed = __shfl_sync(0xffffffffu, pL, src);
+        const float2 yprev = make_float2(__shfl_sync(0xffffffffu, yL.x, src), __shfl_sync(0xffffffffu, yL.y, src));
         float w[2 * W];
 #pragma unroll
         for (int q = 0; q < 2 * W; ++q) w[q] = __shfl_sync(0xffffffffu, wL[q], src);
@@ -447,26 +453,21 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
           tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
         }
         float2 v = make_float2(tot.x * a.scale, tot.y * a.scale);
+        if (a.accumulate) {
+          v.x += yprev.x;
+          v.y += yprev.y;
+        } else if (a.y_meas) {
+          v.x -= yprev.x;
+          v.y -= yprev.y;
+        }
         if (valid && sub == 0) {
-          if (a.accumulate) {
-            const float2 old = a.y[m];
-            v.x += old.x;
-            v.y += old.y;
-          } else if (a.y_meas) {
-            const float2 ym = __ldg(&a.y_meas[m]);
-            v.x -= ym.x;
-            v.y -= ym.y;
-          }
           a.y[m] = v;
           sumsq = fmaf(v.x, v.x, fmaf(v.y, v.y, sumsq));
         }
-        if (a.contrib) {
-          v.x = __shfl_sync(0xffffffffu, v.x, slot * LPS);
-          v.y = __shfl_sync(0xffffffffu, v.y, slot * LPS);
-          if (valid) {
-            const float2 c0 = cmulcf(P0, v), c1 = cmulcf(P1, v);
-            reinterpret_cast<float4*>(a.contrib + (size_t)m * CS)[sub] = make_float4(c0.x, c0.y, c1.x, c1.y);
-          }
+        if (a.contrib && valid) {
+          // every lane of the sample holds the same reduced value
+          const float2 c0 = cmulcf(P0, v), c1 = cmulcf(P1, v);
+          reinterpret_cast<float4*>(a.contrib + (size_t)m * CS)[sub] = make_float4(c0.x, c0.y, c1.x, c1.y);
         }
       }
       __syncwarp();

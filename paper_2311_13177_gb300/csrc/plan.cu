@@ -382,7 +382,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   // their first tap), ascending m within a tile; every non-empty tile's run is
   // cut into items of at most kInterpItem samples.  One CTA per item stages
   // the tile plus its (W-1)-cell halo in shared memory.
-  p->interp_tile = p->cs <= 32 ? 16 : 8;
+  p->interp_tile = interp_tile_for(p->cs, p->W);
   const int TI = p->interp_tile;
   const int tps = n / TI;
   const size_t ntile = (size_t)p->T * tps * tps;
@@ -715,7 +715,7 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
   const size_t W = d->kb_width == 8 ? 8 : 6;
   const size_t chunk = d->bin_chunk == 0 ? std::min<size_t>(Nf, kMaxChunk) : std::min<size_t>(d->bin_chunk, Nf);
   const size_t cs = chunk + (chunk & 1);
-  const size_t TI = cs <= 32 ? 16 : 8;
+  const size_t TI = (size_t)interp_tile_for((int)cs, (int)W);
   const size_t ncell = T * n * n;
   const size_t vol = T * N * N * Nf;
   const size_t interp_items = M / kInterpItem + T * (n / TI) * (n / TI) + 1;

@@ -25,6 +25,16 @@ constexpr int kSpreadGroupPatch = 4;   // groups are ordered in 4 x 4-group patc
 constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list entries
 constexpr int kSpreadGroupItemCost = 2048;  // target work per grouped spread item
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
+
+// Interpolation tile edge (cells) for bin stride cs and kernel width W: 16
+// up to 32 bins, else 8.  At width 8 with 32 bins the 16-cell tile plus its
+// 7-cell halo (135 KB) leaves room for one buffer only, so its copy does not
+// overlap the previous tile's work; an 8-cell tile double-buffers but stages
+// 3.5x the cells it owns instead of 2.1x and splits the samples into items a
+// quarter the size, and measured slower (90 against 82 us at the static
+// workload).
+constexpr int interp_tile_for(int cs, int W) { return (void)W, cs <= 32 ? 16 : 8; }
+
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
 
 // Status plumbing -----------------------------------------------------------

@@ -45,9 +45,8 @@ constexpr int kKpThreads = 256;
 constexpr int kKpPlanes = 6;
 constexpr int kKpMaxScales = 2;
 constexpr int kKpMaxF = 16;
-constexpr int kKpMaxQ = kKpMaxScales * kKpMaxF;  // 32
-constexpr int kKpYChunk = 8;                      // image rows per partial of Xsum
-constexpr int kKpXBlock = 64;                     // columns per shared-memory block in the Xsum kernel
+constexpr int kKpYChunk = 8;                      // image rows per CTA of the gradient kernels
+constexpr int kKpTB = 8;                          // frames (or rows) staged per barrier
 
 enum { kXY = 0, kXW = 1, kXT = 2, kYW = 3, kYT = 4, kWT = 5 };
 
@@ -221,11 +220,13 @@ __global__ void __launch_bounds__(kKpThreads) kp_contract_kernel(const float2* _
 // --- render ------------------------------------------------------------------
 
 // CTA = (column strip of XS image columns, image row y); thread = (column x,
-// bin w) with w fastest; the CTA walks the frames, each frame's Eyt Ewt and
-// Ext values staged in shared memory (double-buffered, one barrier a frame).
+// bin w) with w fastest; the CTA walks the frames TB at a time: the
+// frames' Eyt Ewt (laid out [frame][q][w]) and Ext ([frame][q][x]) are staged
+// in shared memory with one barrier per batch (double-buffered), so each
+// thread has TB independent loads in flight per fill; conflict-free reads.
 template <int QM>
 __global__ void __launch_bounds__(kKpThreads) kp_render_kernel(const float2* __restrict__ E, KpArgs a, int XS,
-                                                               float2* __restrict__ V) {
+                                                               int TB, float2* __restrict__ V) {
   extern __shared__ float2 kp_sm[];
   grid_dep_wait();
   grid_dep_release();
@@ -249,244 +250,296 @@ __global__ void __launch_bounds__(kKpThreads) kp_render_kernel(const float2* __r
       R[q] = kmul(kmul(A[q], Exy[((size_t)y * N + x) * Q + q]),
                   kmul(Exw[((size_t)x * Nf + w) * Q + q], Eyw[((size_t)y * Nf + w) * Q + q]));
   }
-  const int hsz = Nf * Q, usz = XS * Q;
-  for (int t = 0; t < a.T; ++t) {
-    float2* H = kp_sm + (t & 1) * (hsz + usz);
-    float2* U = H + hsz;
+  const int hsz = Nf * Q, usz = XS * Q, bsz = TB * (hsz + usz);
+  for (int t0 = 0, buf = 0; t0 < a.T; t0 += TB, buf ^= 1) {
+    const int nt = min(TB, a.T - t0);
+    float2* H = kp_sm + buf * bsz;       // [frame][q][w]
+    float2* U = H + TB * hsz;            // [frame][q][x]
     for (int e = threadIdx.x; e < hsz; e += blockDim.x) {
-      const int ww = e / Q, q = e - ww * Q;
-      H[e] = kmul(Eyt[((size_t)t * N + y) * Q + q], Ewt[((size_t)t * Nf + ww) * Q + q]);
+      const int ww = e % Nf, q = e / Nf;
+      for (int tb = 0; tb < nt; ++tb)
+        H[tb * hsz + e] = kmul(Eyt[((size_t)(t0 + tb) * N + y) * Q + q], Ewt[((size_t)(t0 + tb) * Nf + ww) * Q + q]);
     }
     for (int e = threadIdx.x; e < usz; e += blockDim.x) {
-      const int xx = blockIdx.x * XS + e / Q;
-      U[e] = xx < N ? Ext[((size_t)t * N + xx) * Q + (e % Q)] : make_float2(0.f, 0.f);
+      const int xx = blockIdx.x * XS + e % XS, q = e / XS;
+      for (int tb = 0; tb < nt; ++tb)
+        U[tb * usz + e] = xx < N ? Ext[((size_t)(t0 + tb) * N + xx) * Q + q] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    if (valid) {
-      float2 acc = make_float2(0.f, 0.f);
+    if (valid)
+      for (int tb = 0; tb < nt; ++tb) {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < QM; ++q)
-        if (q < Q) {
-          const float2 z = kmul(R[q], kmul(U[xl * Q + q], H[w * Q + q]));
-          acc = kadd(acc, z);
-        }
-      V[(((size_t)t * N + y) * N + x) * Nf + w] = acc;
-    }
+        for (int q = 0; q < QM; ++q)
+          if (q < Q) acc = kadd(acc, kmul(R[q], kmul(U[tb * usz + q * XS + xl], H[tb * hsz + q * Nf + w])));
+        V[((((size_t)t0 + tb) * N + y) * N + x) * Nf + w] = acc;
+      }
   }
 }
 
-// --- gradient partial sums --------------------------------------------------
+// --- gradients ---------------------------------------------------------------
+//
+// Three kernels walk the frames over tiles of the volume and leave small
+// fixed-order partials (summed afterwards in index order by kp_sum_kernel):
+//   W kernel, CTA (strip of XS columns, chunk of kKpYChunk rows), thread (x, q):
+//     Wsum(t, y, x)_q = sum_w conj(A Eyw Ewt Exw)_q g, then
+//     dExy(y, x) = sum_t conj(Ext Eyt) Wsum           complete (one CTA owns (y, x))
+//     dExt(t, x) = sum_y conj(Exy Eyt) Wsum           partial per row chunk
+//     dEyt(t, y) = sum_x conj(Exy Ext) Wsum           partial per column strip
+//   T kernel, CTA (strip, row chunk), thread (x, w):
+//     Tsum(y, x, w)_q = sum_t conj(Exy Ext Eyt Ewt)_q g, then
+//     dExw(x, w) = sum_y conj(A Eyw) Tsum             partial per row chunk
+//     dEyw(y, w) = sum_x conj(A Exw) Tsum             partial per column strip
+//   X kernel, CTA (strip, frame t), thread (w, q):
+//     Xsum(t, w)_q = sum_y conj(Eyw) sum_x conj(Exw Exy Ext Eyt)_q g
+//                                                     partial per column strip
+//   then dEwt = conj(A) Xsum and dA = sum_(t, w) conj(Ewt) Xsum.
 
-// Wsum[t][y][x][q] = sum_w conj(A Eyw Ewt Exw)_q g(t, y, x, w); CTA per (t, y)
-// with C[w][q] = A Eyw(y, w) Ewt(t, w) in shared memory.
-__global__ void __launch_bounds__(kKpThreads) kp_wsum_kernel(const float2* __restrict__ E, KpArgs a,
-                                                             const float2* __restrict__ gV, float2* __restrict__ Ws) {
+struct KpPart {
+  float2* xt;   // [ychunks][T][N][Q]
+  float2* yt;   // [xstrips_W][T][N][Q]
+  float2* xw;   // [ychunks][N][Nf][Q]
+  float2* yw;   // [xstrips_T][N][Nf][Q]
+  float2* wt;   // [xstrips_X][T][Nf][Q]
+};
+
+__global__ void __launch_bounds__(kKpThreads) kp_wgrad_kernel(const float2* __restrict__ E, KpArgs a, int XS,
+                                                              int YBW, const float2* __restrict__ gV, float2* __restrict__ dE,
+                                                              KpPart part) {
   extern __shared__ float2 kp_sm[];
   grid_dep_wait();
   grid_dep_release();
   const int Q = a.Q, Nf = a.Nf, N = a.N;
-  const int t = blockIdx.x, y = blockIdx.y;
+  const int xl = threadIdx.x / Q, q = threadIdx.x - xl * Q;
+  const int x = blockIdx.x * XS + xl;
+  const bool valid = xl < XS && x < N;
+  const int y0 = blockIdx.y * kKpYChunk, ny = min(kKpYChunk, N - y0);
+  const float2* Exy = E + a.e_off[kXY];
   const float2* Exw = E + a.e_off[kXW];
+  const float2* Ext = E + a.e_off[kXT];
   const float2* Eyw = E + a.e_off[kYW];
+  const float2* Eyt = E + a.e_off[kYT];
   const float2* Ewt = E + a.e_off[kWT];
   const float2* A = E + a.e_off[kKpPlanes];
-  for (int e = threadIdx.x; e < Nf * Q; e += blockDim.x) {
-    const int w = e / Q, q = e - w * Q;
-    kp_sm[e] = kmul(A[q], kmul(Eyw[((size_t)y * Nf + w) * Q + q], Ewt[((size_t)t * Nf + w) * Q + q]));
+  float2* sEw = kp_sm;                            // [w][xl][q] Exw of the strip
+  float2* sC = sEw + (size_t)Nf * XS * Q;         // [row][w][q] A Eyw(y) Ewt(t) of YBW rows of the current frame
+  float2* sR = sC + (size_t)YBW * Nf * Q;         // [yi][xl][q] dEyt terms of the current frame
+  for (int e = threadIdx.x; e < Nf * XS * Q; e += blockDim.x) {
+    const int qq = e % Q, r = e / Q, xx = r % XS, ww = r / XS;
+    const int gx = blockIdx.x * XS + xx;
+    sEw[e] = gx < N ? Exw[((size_t)gx * Nf + ww) * Q + qq] : make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  const float2* g = gV + ((size_t)t * N + y) * N * Nf;
-  float2* out = Ws + ((size_t)t * N + y) * N * Q;
-  for (int e = threadIdx.x; e < N * Q; e += blockDim.x) {
-    const int x = e / Q, q = e - x * Q;
-    const float2* ew = Exw + (size_t)x * Nf * Q + q;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int w = 0; w < Nf; ++w) acc = kadd(acc, kcmul(kmul(kp_sm[w * Q + q], ew[(size_t)w * Q]), g[(size_t)x * Nf + w]));
-    out[e] = acc;
+  float2 dxy[kKpYChunk], exy[kKpYChunk];
+#pragma unroll
+  for (int i = 0; i < kKpYChunk; ++i) {
+    dxy[i] = make_float2(0.f, 0.f);
+    exy[i] = (valid && i < ny) ? Exy[((size_t)(y0 + i) * N + x) * Q + q] : make_float2(0.f, 0.f);
   }
+  for (int t = 0; t < a.T; ++t) {
+    float2 dxt = make_float2(0.f, 0.f);
+    const float2 ext = valid ? Ext[((size_t)t * N + x) * Q + q] : make_float2(0.f, 0.f);
+    for (int yb = 0; yb < ny; yb += YBW) {
+      const int nb = min(YBW, ny - yb);
+      // the frame's A Eyw Ewt for YBW rows of the chunk, one barrier
+      for (int e = threadIdx.x; e < Nf * Q; e += blockDim.x) {
+        const int ww = e / Q, qq = e - ww * Q;
+        const float2 aw = kmul(A[qq], Ewt[((size_t)t * Nf + ww) * Q + qq]);
+        for (int r = 0; r < nb; ++r) sC[r * Nf * Q + e] = kmul(aw, Eyw[((size_t)(y0 + yb + r) * Nf + ww) * Q + qq]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int yi = 0; yi < kKpYChunk; ++yi) {
+        if (yi < yb || yi >= yb + nb) continue;
+        const int y = y0 + yi;
+        if (valid) {
+          const float2* g = gV + (((size_t)t * N + y) * N + x) * Nf;
+          const float2* C = sC + (size_t)(yi - yb) * Nf * Q;
+          float2 ws = make_float2(0.f, 0.f);
+          for (int ww = 0; ww < Nf; ++ww)
+            ws = kadd(ws, kcmul(kmul(C[ww * Q + q], sEw[((size_t)ww * XS + xl) * Q + q]), g[ww]));
+          const float2 eyt = Eyt[((size_t)t * N + y) * Q + q];
+          dxy[yi] = kadd(dxy[yi], kcmul(kmul(ext, eyt), ws));
+          dxt = kadd(dxt, kcmul(kmul(exy[yi], eyt), ws));
+          sR[((size_t)yi * XS + xl) * Q + q] = kcmul(kmul(exy[yi], ext), ws);
+        } else if (xl < XS) {
+          sR[((size_t)yi * XS + xl) * Q + q] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();  // sC is refilled for the next rows
+    }
+    // dEyt partial of this strip: sum the columns' terms in column order
+    for (int e = threadIdx.x; e < ny * Q; e += blockDim.x) {
+      const int yi = e / Q, qq = e - yi * Q;
+      float2 s = make_float2(0.f, 0.f);
+      for (int xx = 0; xx < XS; ++xx) s = kadd(s, sR[((size_t)yi * XS + xx) * Q + qq]);
+      part.yt[(((size_t)blockIdx.x * a.T + t) * N + y0 + yi) * Q + qq] = s;
+    }
+    if (valid) part.xt[(((size_t)blockIdx.y * a.T + t) * N + x) * Q + q] = dxt;
+    __syncthreads();  // sC and sR are rewritten for the next frame
+  }
+  if (valid)
+    for (int yi = 0; yi < ny; ++yi) dE[a.e_off[kXY] + ((size_t)(y0 + yi) * N + x) * Q + q] = dxy[yi];
 }
 
-// Tsum[y][x][w][q] = sum_t conj(Ewt(t, w) U3(t, y, x))_q g(t, y, x, w),
-// U3 = Exy Ext Eyt; CTA = (column strip, row y), thread = (x, w), the frames
-// walked with U3 and Ewt of each frame in shared memory.
 template <int QM>
-__global__ void __launch_bounds__(kKpThreads) kp_tsum_kernel(const float2* __restrict__ E, KpArgs a, int XS,
-                                                             const float2* __restrict__ gV, float2* __restrict__ Ts) {
+__global__ void __launch_bounds__(kKpThreads) kp_tgrad_kernel(const float2* __restrict__ E, KpArgs a, int XS, int TB,
+                                                              const float2* __restrict__ gV, KpPart part) {
   extern __shared__ float2 kp_sm[];
   grid_dep_wait();
   grid_dep_release();
   const int Q = a.Q, Nf = a.Nf, N = a.N;
-  const int y = blockIdx.y;
   const int xl = threadIdx.x / Nf, w = threadIdx.x - xl * Nf;
   const int x = blockIdx.x * XS + xl;
   const bool valid = xl < XS && x < N;
+  const int y0 = blockIdx.y * kKpYChunk, ny = min(kKpYChunk, N - y0);
   const float2* Exy = E + a.e_off[kXY];
+  const float2* Exw = E + a.e_off[kXW];
   const float2* Ext = E + a.e_off[kXT];
+  const float2* Eyw = E + a.e_off[kYW];
   const float2* Eyt = E + a.e_off[kYT];
   const float2* Ewt = E + a.e_off[kWT];
-  float2 acc[QM];
+  const float2* A = E + a.e_off[kKpPlanes];
+  const int hsz = Nf * Q, usz = XS * Q, bsz = TB * (hsz + usz);
+  float2* sR = kp_sm + 2 * (size_t)bsz;  // [q][xl][w] dEyw terms of the current row
+  float2 dxw[QM];
 #pragma unroll
-  for (int q = 0; q < QM; ++q) acc[q] = make_float2(0.f, 0.f);
-  const int hsz = Nf * Q, usz = XS * Q;
-  for (int t = 0; t < a.T; ++t) {
-    float2* H = kp_sm + (t & 1) * (hsz + usz);
-    float2* U = H + hsz;
-    for (int e = threadIdx.x; e < hsz; e += blockDim.x) H[e] = Ewt[(size_t)t * Nf * Q + e];
-    for (int e = threadIdx.x; e < usz; e += blockDim.x) {
-      const int xx = blockIdx.x * XS + e / Q, q = e % Q;
-      U[e] = xx < N ? kmul(kmul(Exy[((size_t)y * N + xx) * Q + q], Ext[((size_t)t * N + xx) * Q + q]),
-                           Eyt[((size_t)t * N + y) * Q + q])
-                    : make_float2(0.f, 0.f);
+  for (int qq = 0; qq < QM; ++qq) dxw[qq] = make_float2(0.f, 0.f);
+  int buf = 0;
+  for (int yi = 0; yi < ny; ++yi) {
+    const int y = y0 + yi;
+    float2 acc[QM];
+#pragma unroll
+    for (int qq = 0; qq < QM; ++qq) acc[qq] = make_float2(0.f, 0.f);
+    for (int t0 = 0; t0 < a.T; t0 += TB, buf ^= 1) {
+      const int nt = min(TB, a.T - t0);
+      float2* H = kp_sm + buf * bsz;  // [frame][q][w] Ewt(t)
+      float2* U = H + TB * hsz;       // [frame][q][x] Exy Ext Eyt
+      for (int e = threadIdx.x; e < hsz; e += blockDim.x) {
+        const int ww = e % Nf, qq = e / Nf;
+        for (int tb = 0; tb < nt; ++tb) H[tb * hsz + e] = Ewt[((size_t)(t0 + tb) * Nf + ww) * Q + qq];
+      }
+      for (int e = threadIdx.x; e < usz; e += blockDim.x) {
+        const int xx = blockIdx.x * XS + e % XS, qq = e / XS;
+        const float2 exy = xx < N ? Exy[((size_t)y * N + xx) * Q + qq] : make_float2(0.f, 0.f);
+        for (int tb = 0; tb < nt; ++tb) {
+          const int t = t0 + tb;
+          U[tb * usz + e] = xx < N ? kmul(kmul(exy, Ext[((size_t)t * N + xx) * Q + qq]), Eyt[((size_t)t * N + y) * Q + qq])
+                                   : make_float2(0.f, 0.f);
+        }
+      }
+      __syncthreads();
+      if (valid)
+        for (int tb = 0; tb < nt; ++tb) {
+          const float2 g = gV[((((size_t)t0 + tb) * N + y) * N + x) * Nf + w];
+#pragma unroll
+          for (int qq = 0; qq < QM; ++qq)
+            if (qq < Q) acc[qq] = kadd(acc[qq], kcmul(kmul(H[tb * hsz + qq * Nf + w], U[tb * usz + qq * XS + xl]), g));
+        }
     }
+    // this row's Tsum is in acc: fold it into the dExw chunk partial and
+    // leave the dEyw terms for the column-order sum below
+#pragma unroll
+    for (int qq = 0; qq < QM; ++qq)
+      if (qq < Q) {
+        float2 ta = make_float2(0.f, 0.f), tb = make_float2(0.f, 0.f);
+        if (valid) {
+          ta = kcmul(kmul(A[qq], Eyw[((size_t)y * Nf + w) * Q + qq]), acc[qq]);
+          tb = kcmul(kmul(A[qq], Exw[((size_t)x * Nf + w) * Q + qq]), acc[qq]);
+        }
+        dxw[qq] = kadd(dxw[qq], ta);
+        if (xl < XS) sR[((size_t)qq * XS + xl) * Nf + w] = tb;
+      }
     __syncthreads();
-    if (valid) {
-      const float2 g = gV[(((size_t)t * N + y) * N + x) * Nf + w];
-#pragma unroll
-      for (int q = 0; q < QM; ++q)
-        if (q < Q) acc[q] = kadd(acc[q], kcmul(kmul(H[w * Q + q], U[xl * Q + q]), g));
+    for (int e = threadIdx.x; e < Nf * Q; e += blockDim.x) {
+      const int qq = e / Nf, ww = e - qq * Nf;  // consecutive threads read consecutive bins
+      float2 s = make_float2(0.f, 0.f);
+      for (int xx = 0; xx < XS; ++xx) s = kadd(s, sR[((size_t)qq * XS + xx) * Nf + ww]);
+      part.yw[(((size_t)blockIdx.x * N + y) * Nf + ww) * Q + qq] = s;
     }
+    __syncthreads();  // sR is rewritten for the next row
   }
   if (valid) {
-    float2* out = Ts + (((size_t)y * N + x) * Nf + w) * Q;
+    float2* out = part.xw + (((size_t)blockIdx.y * N + x) * Nf + w) * Q;
 #pragma unroll
-    for (int q = 0; q < QM; ++q)
-      if (q < Q) out[q] = acc[q];
+    for (int qq = 0; qq < QM; ++qq)
+      if (qq < Q) out[qq] = dxw[qq];
   }
 }
 
-// Xpart[c][t][w][q] = sum over the rows y of chunk c of conj(Eyw(y, w))_q
-// sum_x conj(Exw(x, w) U3(t, y, x))_q g(t, y, x, w); CTA per (t, chunk),
-// thread per (w, q), U3 of a block of columns in shared memory.
-__global__ void __launch_bounds__(kKpThreads) kp_xsum_kernel(const float2* __restrict__ E, KpArgs a,
-                                                             const float2* __restrict__ gV, float2* __restrict__ Xp) {
-  __shared__ float2 U[kKpXBlock * kKpMaxQ];
+__global__ void __launch_bounds__(kKpThreads) kp_xgrad_kernel(const float2* __restrict__ E, KpArgs a, int XS, int YB,
+                                                              const float2* __restrict__ gV, KpPart part) {
+  extern __shared__ float2 kp_sm[];
   grid_dep_wait();
   grid_dep_release();
   const int Q = a.Q, Nf = a.Nf, N = a.N;
-  const int t = blockIdx.x, chunk = blockIdx.y;
+  const int t = blockIdx.y;
+  const int x0 = blockIdx.x * XS, nx = min(XS, N - x0);
   const float2* Exy = E + a.e_off[kXY];
   const float2* Exw = E + a.e_off[kXW];
   const float2* Ext = E + a.e_off[kXT];
   const float2* Eyw = E + a.e_off[kYW];
   const float2* Eyt = E + a.e_off[kYT];
+  // per staged row: U [xl][q] = Exy Ext Eyt, G [xl][w] = grad V, Y [w][q] = Eyw
+  const int usz = XS * Q, gsz = XS * Nf, ysz = Nf * Q, rsz = usz + gsz + ysz;
+  float2* sEw = kp_sm;                          // [xl][w][q] Exw of the strip
+  float2* sB = sEw + (size_t)XS * Nf * Q;       // 2 x YB staged rows
+  for (int e = threadIdx.x; e < nx * Nf * Q; e += blockDim.x) sEw[e] = Exw[(size_t)x0 * Nf * Q + e];
   const int npair = Nf * Q;
-  const int y0 = chunk * kKpYChunk, y1 = min(N, y0 + kKpYChunk);
   for (int pb = 0; pb < npair; pb += blockDim.x) {  // (w, q) pairs of this pass
     const int e = pb + threadIdx.x;
     const bool own = e < npair;
-    const int w = own ? e / Q : 0, q = own ? e - (e / Q) * Q : 0;
+    const int w = own ? e / Q : 0, q = own ? e - w * Q : 0;
     float2 acc = make_float2(0.f, 0.f);
-    for (int y = y0; y < y1; ++y) {
-      float2 sx = make_float2(0.f, 0.f);
-      for (int xb = 0; xb < N; xb += kKpXBlock) {
-        const int nx = min(kKpXBlock, N - xb);
-        __syncthreads();
-        for (int u = threadIdx.x; u < nx * Q; u += blockDim.x) {
-          const int xx = xb + u / Q, qq = u % Q;
-          U[u] = kmul(kmul(Exy[((size_t)y * N + xx) * Q + qq], Ext[((size_t)t * N + xx) * Q + qq]),
-                      Eyt[((size_t)t * N + y) * Q + qq]);
-        }
-        __syncthreads();
-        if (own) {
-          const float2* g = gV + (((size_t)t * N + y) * N + xb) * Nf + w;
-          const float2* ew = Exw + ((size_t)xb * Nf + w) * Q + q;
-          for (int xx = 0; xx < nx; ++xx)
-            sx = kadd(sx, kcmul(kmul(ew[(size_t)xx * Nf * Q], U[xx * Q + q]), g[(size_t)xx * Nf]));
+    int buf = 0;
+    for (int yb = 0; yb < N; yb += YB, buf ^= 1) {
+      const int nyb = min(YB, N - yb);
+      float2* Bf = sB + (size_t)buf * YB * rsz;
+      for (int u = threadIdx.x; u < nx * Q; u += blockDim.x) {
+        const int xx = x0 + u / Q, qq = u % Q;
+        const float2 ext = Ext[((size_t)t * N + xx) * Q + qq];
+        for (int r = 0; r < nyb; ++r) {
+          const int y = yb + r;
+          Bf[(size_t)r * rsz + u] = kmul(kmul(Exy[((size_t)y * N + xx) * Q + qq], ext), Eyt[((size_t)t * N + y) * Q + qq]);
         }
       }
-      if (own) acc = kadd(acc, kcmul(Eyw[((size_t)y * Nf + w) * Q + q], sx));
+      for (int u = threadIdx.x; u < nx * Nf; u += blockDim.x)
+        for (int r = 0; r < nyb; ++r)
+          Bf[(size_t)r * rsz + usz + u] = gV[(((size_t)t * N + yb + r) * N + x0) * Nf + u];
+      for (int u = threadIdx.x; u < ysz; u += blockDim.x)
+        for (int r = 0; r < nyb; ++r) Bf[(size_t)r * rsz + usz + gsz + u] = Eyw[(size_t)(yb + r) * Nf * Q + u];
+      __syncthreads();
+      if (own)
+        for (int r = 0; r < nyb; ++r) {
+          const float2* Ur = Bf + (size_t)r * rsz;
+          const float2* Gr = Ur + usz;
+          float2 sx = make_float2(0.f, 0.f);
+          for (int xx = 0; xx < nx; ++xx)
+            sx = kadd(sx, kcmul(kmul(sEw[((size_t)xx * Nf + w) * Q + q], Ur[xx * Q + q]), Gr[xx * Nf + w]));
+          acc = kadd(acc, kcmul(Gr[gsz + w * Q + q], sx));
+        }
     }
-    if (own) Xp[(((size_t)chunk * a.T + t) * Nf + w) * Q + q] = acc;
+    if (own) part.wt[(((size_t)blockIdx.x * a.T + t) * Nf + w) * Q + q] = acc;
+    __syncthreads();
   }
 }
 
-// Second passes: the expanded gradients, each a fixed-order sum.
-// dExy[y][x][q] = sum_t conj(Ext(t, x) Eyt(t, y)) Wsum(t, y, x)
-__global__ void __launch_bounds__(kKpThreads) kp_dxy_kernel(const float2* __restrict__ E, KpArgs a,
-                                                            const float2* __restrict__ Ws, float2* __restrict__ dE) {
+// out[i] = scale(i) * sum_c part[c * len + i] over c = 0 .. nparts - 1 in
+// order; scale = conj(A[i % Q]) when conj_a, else 1.
+__global__ void __launch_bounds__(kKpThreads) kp_sum_kernel(const float2* __restrict__ part, int nparts, size_t len,
+                                                            const float2* __restrict__ A, int Q, int conj_a,
+                                                            float2* __restrict__ out) {
   grid_dep_wait();
   grid_dep_release();
-  const int Q = a.Q, N = a.N;
-  const size_t total = (size_t)N * N * Q;
-  const float2* Ext = E + a.e_off[kXT];
-  const float2* Eyt = E + a.e_off[kYT];
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int q = (int)(i % Q);
-    const size_t yx = i / Q;
-    const int x = (int)(yx % N), y = (int)(yx / N);
-    float2 acc = make_float2(0.f, 0.f);
-    for (int t = 0; t < a.T; ++t)
-      acc = kadd(acc, kcmul(kmul(Ext[((size_t)t * N + x) * Q + q], Eyt[((size_t)t * N + y) * Q + q]),
-                            Ws[(size_t)t * total + i]));
-    dE[a.e_off[kXY] + i] = acc;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int c = 0; c < nparts; ++c) s = kadd(s, part[(size_t)c * len + i]);
+    out[i] = conj_a ? kcmul(A[i % Q], s) : s;
   }
 }
 
-// dExt[t][x][q] = sum_y conj(Exy(y, x) Eyt(t, y)) Wsum(t, y, x);
-// dEyt[t][y][q] = sum_x conj(Exy(y, x) Ext(t, x)) Wsum(t, y, x).
-__global__ void __launch_bounds__(kKpThreads) kp_dt_kernel(const float2* __restrict__ E, KpArgs a,
-                                                           const float2* __restrict__ Ws, float2* __restrict__ dE) {
-  grid_dep_wait();
-  grid_dep_release();
-  const int Q = a.Q, N = a.N;
-  const size_t per = (size_t)a.T * N * Q;  // elements of dExt (= of dEyt)
-  const float2* Exy = E + a.e_off[kXY];
-  const float2* Ext = E + a.e_off[kXT];
-  const float2* Eyt = E + a.e_off[kYT];
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * per; i += (size_t)gridDim.x * blockDim.x) {
-    const bool is_xt = i < per;
-    const size_t j = is_xt ? i : i - per;
-    const int q = (int)(j % Q);
-    const size_t tr = j / Q;
-    const int r = (int)(tr % N), t = (int)(tr / N);  // r = x (dExt) or y (dEyt)
-    float2 acc = make_float2(0.f, 0.f);
-    if (is_xt) {
-      for (int y = 0; y < N; ++y)
-        acc = kadd(acc, kcmul(kmul(Exy[((size_t)y * N + r) * Q + q], Eyt[((size_t)t * N + y) * Q + q]),
-                              Ws[(((size_t)t * N + y) * N + r) * Q + q]));
-      dE[a.e_off[kXT] + j] = acc;
-    } else {
-      for (int x = 0; x < N; ++x)
-        acc = kadd(acc, kcmul(kmul(Exy[((size_t)r * N + x) * Q + q], Ext[((size_t)t * N + x) * Q + q]),
-                              Ws[(((size_t)t * N + r) * N + x) * Q + q]));
-      dE[a.e_off[kYT] + j] = acc;
-    }
-  }
-}
-
-// dExw[x][w][q] = sum_y conj(A Eyw(y, w)) Tsum(y, x, w);
-// dEyw[y][w][q] = sum_x conj(A Exw(x, w)) Tsum(y, x, w).
-__global__ void __launch_bounds__(kKpThreads) kp_dw_kernel(const float2* __restrict__ E, KpArgs a,
-                                                           const float2* __restrict__ Ts, float2* __restrict__ dE) {
-  grid_dep_wait();
-  grid_dep_release();
-  const int Q = a.Q, N = a.N, Nf = a.Nf;
-  const size_t per = (size_t)N * Nf * Q;
-  const float2* Exw = E + a.e_off[kXW];
-  const float2* Eyw = E + a.e_off[kYW];
-  const float2* A = E + a.e_off[kKpPlanes];
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * per; i += (size_t)gridDim.x * blockDim.x) {
-    const bool is_xw = i < per;
-    const size_t j = is_xw ? i : i - per;
-    const int q = (int)(j % Q);
-    const size_t rw = j / Q;
-    const int w = (int)(rw % Nf), r = (int)(rw / Nf);  // r = x (dExw) or y (dEyw)
-    float2 acc = make_float2(0.f, 0.f);
-    if (is_xw) {
-      for (int y = 0; y < N; ++y)
-        acc = kadd(acc, kcmul(Eyw[((size_t)y * Nf + w) * Q + q], Ts[(((size_t)y * N + r) * Nf + w) * Q + q]));
-      dE[a.e_off[kXW] + j] = kcmul(A[q], acc);
-    } else {
-      for (int x = 0; x < N; ++x)
-        acc = kadd(acc, kcmul(Exw[((size_t)x * Nf + w) * Q + q], Ts[(((size_t)r * N + x) * Nf + w) * Q + q]));
-      dE[a.e_off[kYW] + j] = kcmul(A[q], acc);
-    }
-  }
-}
-
-// dEwt[t][w][q] = conj(A) Xsum(t, w) and dA[q] = sum_(t, w) conj(Ewt(t, w)) Xsum(t, w),
-// Xsum = the chunk partials summed in chunk order.  One CTA per q for dA.
-__global__ void __launch_bounds__(kKpThreads) kp_dwt_kernel(const float2* __restrict__ E, KpArgs a, int nchunks,
+// dEwt[t][w][q] = conj(A) Xsum and dA[q] = sum_(t, w) conj(Ewt(t, w)) Xsum,
+// Xsum = the strip partials summed in strip order.  One CTA per q for dA.
+__global__ void __launch_bounds__(kKpThreads) kp_dwt_kernel(const float2* __restrict__ E, KpArgs a, int nparts,
                                                             const float2* __restrict__ Xp, float2* __restrict__ dE) {
   __shared__ float2 red[kKpThreads];
   grid_dep_wait();
@@ -498,7 +551,7 @@ __global__ void __launch_bounds__(kKpThreads) kp_dwt_kernel(const float2* __rest
   float2 da = make_float2(0.f, 0.f);
   for (int tw = threadIdx.x; tw < a.T * Nf; tw += blockDim.x) {
     float2 xs = make_float2(0.f, 0.f);
-    for (int c = 0; c < nchunks; ++c) xs = kadd(xs, Xp[((size_t)c * a.T * Nf + tw) * Q + q]);
+    for (int c = 0; c < nparts; ++c) xs = kadd(xs, Xp[((size_t)c * a.T * Nf + tw) * Q + q]);
     dE[a.e_off[kWT] + (size_t)tw * Q + q] = kcmul(Aq, xs);
     da = kadd(da, kcmul(Ewt[(size_t)tw * Q + q], xs));
   }
@@ -568,7 +621,7 @@ prop_status kp_check(const Plan& p, int F, int S) {
   if (F < 1 || F > kKpMaxF) return fail(PROP_ERR_INVALID_ARG, "kplanes: features must be in [1, 16]");
   if (S < 1 || S > kKpMaxScales) return fail(PROP_ERR_INVALID_ARG, "kplanes: scales must be 1 or 2");
   if ((p.N >> (S - 1)) < 2) return fail(PROP_ERR_INVALID_ARG, "kplanes: image too small for the scales");
-  if (p.Nf > kKpThreads) return fail(PROP_ERR_INVALID_ARG, "kplanes: at most 256 spectral bins");
+  if (p.Nf > 64) return fail(PROP_ERR_INVALID_ARG, "kplanes: at most 64 spectral bins");
   return PROP_OK;
 }
 
@@ -576,43 +629,88 @@ unsigned kp_blocks(size_t count, const Plan& p) {
   return (unsigned)std::max<size_t>(1, std::min<size_t>((count + kKpThreads - 1) / kKpThreads, (size_t)16 * p.num_sms));
 }
 
-// Columns per CTA of the render and time-sum kernels: XS * Nf <= 256 threads.
-int kp_strip(const Plan& p) { return std::max(1, std::min(p.N, kKpThreads / p.Nf)); }
+// Tile widths (image columns per CTA) and batch depths (frames or rows
+// staged per barrier) of the frame-walking kernels.
+struct KpTiles {
+  int xs_r, xs_w, xs_t, xs_x;  // render (thread per (x, w)), W (x, q), T (x, w), X (strip in shared memory)
+  int ns_r, ns_w, ns_t, ns_x, nch;  // strips of the render, W, T and X kernels; row chunks
+  int tb_r, tb_t, yb_x, yb_w;   // frames per barrier (render, T), rows per barrier (X, W)
+};
+KpTiles kp_tiles(const Plan& p, int Q) {
+  KpTiles k;
+  const int c8 = (int)sizeof(float2);
+  k.xs_r = std::max(1, std::min(std::min(p.N, 64), kKpThreads / p.Nf));
+  k.xs_t = k.xs_r;
+  k.xs_w = std::max(1, std::min(std::min(p.N, kKpThreads / Q), 8192 / (p.Nf * Q)));
+  k.xs_x = std::max(1, std::min(8, (96 * 1024) / ((p.Nf + 2) * Q * c8)));
+  k.ns_r = (p.N + k.xs_r - 1) / k.xs_r;
+  k.ns_w = (p.N + k.xs_w - 1) / k.xs_w;
+  k.ns_t = (p.N + k.xs_t - 1) / k.xs_t;
+  k.ns_x = (p.N + k.xs_x - 1) / k.xs_x;
+  k.nch = (p.N + kKpYChunk - 1) / kKpYChunk;
+  const int per_frame = 2 * (p.Nf + k.xs_r) * Q * c8;  // double-buffered staging of one frame
+  k.tb_r = std::max(1, std::min(kKpTB, (96 * 1024) / per_frame));
+  k.tb_t = k.tb_r;
+  const int xrow = k.xs_x * Q + k.xs_x * p.Nf + p.Nf * Q;  // one staged row of the X kernel
+  k.yb_x = std::max(1, std::min(kKpTB, (64 * 1024) / (2 * xrow * c8)));
+  k.yb_w = std::max(1, std::min(kKpYChunk, 4096 / (p.Nf * Q)));
+  return k;
+}
+size_t smem_render(const Plan& p, const KpArgs& a, const KpTiles& k) {
+  return 2 * (size_t)k.tb_r * (p.Nf + k.xs_r) * a.Q * sizeof(float2);
+}
+size_t smem_w(const Plan& p, const KpArgs& a, const KpTiles& k) {
+  return ((size_t)p.Nf * k.xs_w * a.Q + (size_t)k.yb_w * p.Nf * a.Q + (size_t)kKpYChunk * k.xs_w * a.Q) *
+         sizeof(float2);
+}
+size_t smem_t(const Plan& p, const KpArgs& a, const KpTiles& k) {
+  return (2 * (size_t)k.tb_t * (p.Nf * a.Q + k.xs_t * a.Q) + (size_t)a.Q * k.xs_t * p.Nf) * sizeof(float2);
+}
+size_t smem_x(const Plan& p, const KpArgs& a, const KpTiles& k) {
+  const size_t row = (size_t)k.xs_x * a.Q + (size_t)k.xs_x * p.Nf + (size_t)p.Nf * a.Q;
+  return ((size_t)k.xs_x * p.Nf * a.Q + 2 * (size_t)k.yb_x * row) * sizeof(float2);
+}
 
-int kp_ychunks(const Plan& p) { return (p.N + kKpYChunk - 1) / kKpYChunk; }
-
-// Device workspace of the model (the expanded planes and the gradient
-// partials), grown on demand and kept in the plan.
+// Device workspace of the model (the expanded planes, their gradients and
+// the gradient kernels' partials), grown on demand and kept in the plan.
 struct KpWork {
   float2* E;     // expanded planes + A
   float2* dE;    // expanded gradients
-  float2* Ws;    // [T][N][N][Q]
-  float2* Ts;    // [N][N][Nf][Q]
-  float2* Xp;    // [chunks][T][Nf][Q]
+  KpPart part;
 };
 
+size_t kp_part_elems(const Plan& p, const KpArgs& a, const KpTiles& k, size_t* off) {
+  const size_t Q = a.Q, N = p.N, Nf = p.Nf, T = p.T;
+  const size_t sz[5] = {k.nch * T * N * Q, k.ns_w * T * N * Q, k.nch * N * Nf * Q, k.ns_t * N * Nf * Q,
+                        k.ns_x * T * Nf * Q};
+  size_t o = 0;
+  for (int i = 0; i < 5; ++i) {
+    if (off) off[i] = o;
+    o += sz[i];
+  }
+  return o;
+}
+
 KpWork kp_carve(const Plan& p, const KpArgs& a) {
+  const KpTiles k = kp_tiles(p, a.Q);
   KpWork w{};
   float2* base = (float2*)p.kp_work;
   w.E = base;
-  base += a.e_count;
-  w.dE = base;
-  base += a.e_count;
-  w.Ws = base;
-  base += (size_t)a.T * a.N * a.N * a.Q;
-  w.Ts = base;
-  base += (size_t)a.N * a.N * a.Nf * a.Q;
-  w.Xp = base;
+  w.dE = base + a.e_count;
+  float2* pb = w.dE + a.e_count;
+  size_t off[5];
+  kp_part_elems(p, a, k, off);
+  w.part.xt = pb + off[0];
+  w.part.yt = pb + off[1];
+  w.part.xw = pb + off[2];
+  w.part.yw = pb + off[3];
+  w.part.wt = pb + off[4];
   return w;
 }
 
-size_t kp_work_elems(const Plan& p, const KpArgs& a) {
-  return 2 * a.e_count + (size_t)a.T * a.N * a.N * a.Q + (size_t)a.N * a.N * a.Nf * a.Q +
-         (size_t)kp_ychunks(p) * a.T * a.Nf * a.Q;
-}
-
 prop_status kp_ensure(Plan& p, const KpArgs& a) {
-  const size_t bytes = kp_work_elems(p, a) * sizeof(float2);
+  const KpTiles k = kp_tiles(p, a.Q);
+  const size_t bytes = (2 * a.e_count + kp_part_elems(p, a, k, nullptr)) * sizeof(float2);
   if (p.kp_work && p.kp_work_bytes >= bytes) return PROP_OK;
   if (p.kp_work) {
     plan_dev_free(&p, p.kp_work);
@@ -632,44 +730,36 @@ prop_status kp_ensure(Plan& p, const KpArgs& a) {
   return PROP_OK;
 }
 
-template <int QM>
-cudaError_t launch_render_q(const Plan& p, const KpArgs& a, const KpWork& w, float2* V, cudaStream_t s) {
-  const int XS = kp_strip(p);
-  const size_t smem = 2 * (size_t)(p.Nf + XS) * a.Q * sizeof(float2);
-  return launch_dep(kp_render_kernel<QM>, dim3((p.N + XS - 1) / XS, p.N), dim3(XS * p.Nf), smem, s,
-                    (const float2*)w.E, a, XS, V);
-}
-
-template <int QM>
-cudaError_t launch_tsum_q(const Plan& p, const KpArgs& a, const KpWork& w, const float2* gV, cudaStream_t s) {
-  const int XS = kp_strip(p);
-  const size_t smem = 2 * (size_t)(p.Nf + XS) * a.Q * sizeof(float2);
-  return launch_dep(kp_tsum_kernel<QM>, dim3((p.N + XS - 1) / XS, p.N), dim3(XS * p.Nf), smem, s,
-                    (const float2*)w.E, a, XS, gV, w.Ts);
-}
-
-// Shared memory above the default 48 KB for the two frame-walking kernels.
+// Shared memory above the default 48 KB for the frame-walking kernels.
 cudaError_t kp_configure(const Plan& p, const KpArgs& a) {
-  const size_t smem = 2 * (size_t)(p.Nf + kp_strip(p)) * a.Q * sizeof(float2);
-  const size_t wsm = (size_t)p.Nf * a.Q * sizeof(float2);
+  const KpTiles k = kp_tiles(p, a.Q);
   cudaError_t e = cudaSuccess;
-  auto opt = [&](const void* k, size_t bytes) {
+  auto opt = [&](const void* f, size_t bytes) {
     if (e == cudaSuccess && bytes > 48 * 1024)
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   };
-  opt((const void*)kp_render_kernel<8>, smem);
-  opt((const void*)kp_render_kernel<16>, smem);
-  opt((const void*)kp_render_kernel<32>, smem);
-  opt((const void*)kp_tsum_kernel<8>, smem);
-  opt((const void*)kp_tsum_kernel<16>, smem);
-  opt((const void*)kp_tsum_kernel<32>, smem);
-  opt((const void*)kp_wsum_kernel, wsm);
+  const size_t sr = smem_render(p, a, k), st = smem_t(p, a, k);
+  opt((const void*)kp_render_kernel<8>, sr);
+  opt((const void*)kp_render_kernel<16>, sr);
+  opt((const void*)kp_render_kernel<32>, sr);
+  opt((const void*)kp_tgrad_kernel<8>, st);
+  opt((const void*)kp_tgrad_kernel<16>, st);
+  opt((const void*)kp_tgrad_kernel<32>, st);
+  opt((const void*)kp_wgrad_kernel, smem_w(p, a, k));
+  opt((const void*)kp_xgrad_kernel, smem_x(p, a, k));
   return e;
 }
 
 cudaError_t kp_expand(Plan& p, const KpArgs& a, const KpWork& w, const float2* P, cudaStream_t s) {
   StageScope sc(p, kStKpRender, s);
   return launch_dep(kp_expand_kernel, dim3(kp_blocks(a.e_count, p)), dim3(kKpThreads), 0, s, P, a, w.E);
+}
+
+template <int QM>
+cudaError_t launch_render_q(const Plan& p, const KpArgs& a, const KpWork& w, float2* V, cudaStream_t s) {
+  const KpTiles k = kp_tiles(p, a.Q);
+  return launch_dep(kp_render_kernel<QM>, dim3(k.ns_r, p.N), dim3(k.xs_r * p.Nf), smem_render(p, a, k), s,
+                    (const float2*)w.E, a, k.xs_r, k.tb_r, V);
 }
 
 cudaError_t kp_render(Plan& p, const KpArgs& a, const KpWork& w, float2* V, cudaStream_t s) {
@@ -679,31 +769,44 @@ cudaError_t kp_render(Plan& p, const KpArgs& a, const KpWork& w, float2* V, cuda
   return launch_render_q<32>(p, a, w, V, s);
 }
 
+template <int QM>
+cudaError_t launch_tgrad_q(const Plan& p, const KpArgs& a, const KpWork& w, const float2* gV, cudaStream_t s) {
+  const KpTiles k = kp_tiles(p, a.Q);
+  return launch_dep(kp_tgrad_kernel<QM>, dim3(k.ns_t, k.nch), dim3(k.xs_t * p.Nf), smem_t(p, a, k), s,
+                    (const float2*)w.E, a, k.xs_t, k.tb_t, gV, w.part);
+}
+
 // Parameter gradients G from grad V, with w.E holding the expanded planes.
 cudaError_t kp_vjp(Plan& p, const KpArgs& a, const KpWork& w, const float2* gV, float2* G, size_t count,
                    cudaStream_t s) {
   StageScope sc(p, kStKpVjp, s);
+  const KpTiles k = kp_tiles(p, a.Q);
+  const float2* A = w.E + a.e_off[kKpPlanes];
   cudaError_t e;
-  const int nch = kp_ychunks(p);
-  e = launch_dep(kp_wsum_kernel, dim3(a.T, a.N), dim3(kKpThreads), (size_t)a.Nf * a.Q * sizeof(float2), s,
-                 (const float2*)w.E, a, gV, w.Ws);
+  e = launch_dep(kp_wgrad_kernel, dim3(k.ns_w, k.nch), dim3(k.xs_w * a.Q), smem_w(p, a, k), s, (const float2*)w.E,
+                 a, k.xs_w, k.yb_w, gV, w.dE, w.part);
   if (e != cudaSuccess) return e;
-  e = a.Q <= 8 ? launch_tsum_q<8>(p, a, w, gV, s)
-               : a.Q <= 16 ? launch_tsum_q<16>(p, a, w, gV, s) : launch_tsum_q<32>(p, a, w, gV, s);
+  e = a.Q <= 8 ? launch_tgrad_q<8>(p, a, w, gV, s)
+               : a.Q <= 16 ? launch_tgrad_q<16>(p, a, w, gV, s) : launch_tgrad_q<32>(p, a, w, gV, s);
   if (e != cudaSuccess) return e;
-  e = launch_dep(kp_xsum_kernel, dim3(a.T, nch), dim3(kKpThreads), 0, s, (const float2*)w.E, a, gV, w.Xp);
+  e = launch_dep(kp_xgrad_kernel, dim3(k.ns_x, p.T), dim3(kKpThreads), smem_x(p, a, k), s, (const float2*)w.E, a,
+                 k.xs_x, k.yb_x, gV, w.part);
   if (e != cudaSuccess) return e;
-  e = launch_dep(kp_dxy_kernel, dim3(kp_blocks((size_t)a.N * a.N * a.Q, p)), dim3(kKpThreads), 0, s,
-                 (const float2*)w.E, a, (const float2*)w.Ws, w.dE);
+  const size_t lxt = (size_t)p.T * p.N * a.Q, lxw = (size_t)p.N * p.Nf * a.Q;
+  e = launch_dep(kp_sum_kernel, dim3(kp_blocks(lxt, p)), dim3(kKpThreads), 0, s, (const float2*)w.part.xt, k.nch,
+                 lxt, A, a.Q, 0, w.dE + a.e_off[kXT]);
   if (e != cudaSuccess) return e;
-  e = launch_dep(kp_dt_kernel, dim3(kp_blocks(2 * (size_t)a.T * a.N * a.Q, p)), dim3(kKpThreads), 0, s,
-                 (const float2*)w.E, a, (const float2*)w.Ws, w.dE);
+  e = launch_dep(kp_sum_kernel, dim3(kp_blocks(lxt, p)), dim3(kKpThreads), 0, s, (const float2*)w.part.yt, k.ns_w,
+                 lxt, A, a.Q, 0, w.dE + a.e_off[kYT]);
   if (e != cudaSuccess) return e;
-  e = launch_dep(kp_dw_kernel, dim3(kp_blocks(2 * (size_t)a.N * a.Nf * a.Q, p)), dim3(kKpThreads), 0, s,
-                 (const float2*)w.E, a, (const float2*)w.Ts, w.dE);
+  e = launch_dep(kp_sum_kernel, dim3(kp_blocks(lxw, p)), dim3(kKpThreads), 0, s, (const float2*)w.part.xw, k.nch,
+                 lxw, A, a.Q, 0, w.dE + a.e_off[kXW]);
   if (e != cudaSuccess) return e;
-  e = launch_dep(kp_dwt_kernel, dim3(a.Q), dim3(kKpThreads), 0, s, (const float2*)w.E, a, nch,
-                 (const float2*)w.Xp, w.dE);
+  e = launch_dep(kp_sum_kernel, dim3(kp_blocks(lxw, p)), dim3(kKpThreads), 0, s, (const float2*)w.part.yw, k.ns_t,
+                 lxw, A, a.Q, 0, w.dE + a.e_off[kYW]);
+  if (e != cudaSuccess) return e;
+  e = launch_dep(kp_dwt_kernel, dim3(a.Q), dim3(kKpThreads), 0, s, (const float2*)w.E, a, k.ns_x,
+                 (const float2*)w.part.wt, w.dE);
   if (e != cudaSuccess) return e;
   return launch_dep(kp_contract_kernel, dim3(kp_blocks(count, p)), dim3(kKpThreads), 0, s, (const float2*)w.dE, a,
                     G, count);

@@ -143,6 +143,26 @@ PROP_API prop_status prop_adjoint(prop_plan plan, const void* y_dev, void* V_dev
 PROP_API prop_status prop_reconstruct(prop_plan plan, const void* y_dev, const prop_recon_params* params,
                              void* V_dev, double* loss_trace_host, void* stream);
 
+/* Several reconstructions advanced together, each stage of an iteration one
+ * launch serving all of them (multi-problem launches whose CTAs are shared
+ * out in proportion to each problem's work; the request server batches its
+ * running requests the same way).  plans[count] (1 <= count <= 8, distinct
+ * handles) must share the transform length 2N, the bin stride (Nf rounded up
+ * to even), the Kaiser-Bessel width and the device, with one bin chunk each;
+ * blade counts, lines, readout lengths, angles, bins, frames and data may
+ * differ.  Problem r runs params[r].iters iterations of prop_reconstruct on
+ * V_dev[r] (in/out) with y_dev[r]; its volume is bitwise that of
+ * prop_reconstruct on its plan alone (the loss trace agrees to FP64
+ * rounding: the |r|^2 block partials are grouped by the CTAs it gets).
+ * loss_trace_host (may be NULL, as may its entries) as in prop_reconstruct;
+ * the call synchronises only when a trace is requested.  Errors:
+ * PROP_ERR_INVALID_ARG (count out of range, null or unaligned buffers, a
+ * plan given twice, plans that cannot share launches, parameters out of
+ * range), PROP_ERR_OOM (optimiser state on first use), PROP_ERR_CUDA. */
+PROP_API prop_status prop_reconstruct_batch(const prop_plan* plans, int count, const void* const* y_dev,
+                                            const prop_recon_params* params, void* const* V_dev,
+                                            double* const* loss_trace_host, void* stream);
+
 /* One Adam iteration of prop_reconstruct, out of place: V_out = the iterate
  * after step k (1-based) from V_in (the two buffers must differ; alternate
  * them between calls).  k == 1 resets the plan's Adam moments; later calls
@@ -238,13 +258,16 @@ PROP_API prop_status prop_psnr(prop_plan plan, const void* image_dev, const void
  * head request when fewer than max_slots requests run and its device
  * footprint (prop_plan_estimate_bytes + its data and volume) fits the budget
  * still free, build its plan inside the arena and upload its data.  A
- * scheduler thread keeps every running request's own stream fed with Adam
- * iterations, so requests that arrive while others run are admitted as soon
- * as a slot and memory free up and their kernels overlap on the GPU.  A
- * request that needs more than the whole budget fails with PROP_ERR_OOM.
- * Results are bitwise identical to a lone prop_reconstruct of the same
- * problem.  Latency = time from prop_serve_submit to the completed copy of
- * the result back to host memory. */
+ * scheduler thread groups the running requests by kernel class (2N, bin
+ * stride, kernel width) and advances each class with batched iterations as
+ * prop_reconstruct_batch does: one launch per stage serves every running
+ * request of the class, whatever its blade count, frames or data; classes
+ * run on their own streams and overlap.  Requests that arrive while others
+ * run join their class's next batched iteration as soon as a slot and memory
+ * free up.  A request that needs more than the whole budget fails with
+ * PROP_ERR_OOM.  Results are bitwise identical to a lone prop_reconstruct of
+ * the same problem.  Latency = time from prop_serve_submit to the completed
+ * copy of the result back to host memory. */
 typedef struct prop_server_s* prop_server;
 typedef uint64_t prop_ticket;
 

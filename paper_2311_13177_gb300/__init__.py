@@ -7,9 +7,9 @@ does, and it raises if the library is missing.
 """
 from .binding import (Plan, ReconParams, ProjParams, prop_plan_create, prop_plan_destroy, prop_plan_workspace_bytes,
                       prop_forward, prop_adjoint, prop_reconstruct, prop_reconstruct_host, prop_loss_grad,
-                      prop_render, prop_psnr)
+                      prop_render, prop_psnr, prop_reconstruct_batch)
 from .autograd import PropOp, prop_apply
 
 __all__ = ["Plan", "ReconParams", "ProjParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
            "prop_forward", "prop_adjoint", "prop_reconstruct", "prop_reconstruct_host", "prop_loss_grad",
-           "prop_render", "prop_psnr", "PropOp", "prop_apply"]
+           "prop_render", "prop_psnr", "prop_reconstruct_batch", "PropOp", "prop_apply"]

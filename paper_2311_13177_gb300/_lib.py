@@ -51,6 +51,9 @@ SIGNATURES = {
     "prop_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "prop_reconstruct": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_void_p,
                                  ctypes.POINTER(c_double), c_void_p]),
+    "prop_reconstruct_batch": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(ReconParamsC), ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(ctypes.POINTER(c_double)), c_void_p]),
     "prop_recon_step": (c_int, [c_void_p, c_void_p, ctypes.POINTER(ReconParamsC), c_int, c_void_p, c_void_p,
                                 c_void_p, c_void_p]),
     "prop_shard_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),

@@ -20,7 +20,7 @@ from ._lib import PlanDesc, ProjParamsC, ReconParamsC, check, lib
 
 __all__ = ["Plan", "ReconParams", "ProjParams", "prop_plan_create", "prop_plan_destroy", "prop_plan_workspace_bytes",
            "prop_forward", "prop_adjoint", "prop_reconstruct", "prop_reconstruct_host",
-           "prop_loss_grad", "prop_render", "prop_psnr"]
+           "prop_loss_grad", "prop_render", "prop_psnr", "prop_reconstruct_batch"]
 
 
 @dataclass
@@ -408,6 +408,30 @@ def prop_render(plan: Plan, V, f_lo=0, f_hi=None, out=None, stream=None):
 
 def prop_psnr(plan: Plan, image, ref, stream=None) -> float:
     return plan.psnr(image, ref, stream)
+
+
+def prop_reconstruct_batch(plans, ys, params, Vs=None, trace=True, stream=None):
+    """prop_reconstruct for several plans of one kernel class at once (shared launches).
+
+    plans: Plan objects (same 2N, bin stride, kernel width); ys: their y tensors; params: one
+    ReconParams each; Vs: start volumes (updated in place; zeros if None).  Returns (Vs, traces)."""
+    n = len(plans)
+    if not (len(ys) == n and len(params) == n):
+        raise ValueError("plans, ys and params must have the same length")
+    if Vs is None:
+        Vs = [torch.zeros(p.vol_shape, dtype=torch.complex64, device=y.device) for p, y in zip(plans, ys)]
+    ptrs = ctypes.c_void_p * n
+    hs = ptrs(*[p.handle.value for p in plans])
+    yp = ptrs(*[_dev_ptr(y, p.data_shape, "y").value for p, y in zip(plans, ys)])
+    vp = ptrs(*[_dev_ptr(V, p.vol_shape, "V").value for p, V in zip(plans, Vs)])
+    pcs = (ReconParamsC * n)(*[q.c() for q in params])
+    traces = [np.zeros(max(q.iters, 1), dtype=np.float64) for q in params] if trace else None
+    tp = None
+    if trace:
+        tp = (ctypes.POINTER(ctypes.c_double) * n)(*[t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                                     for t in traces])
+    check(lib().prop_reconstruct_batch(hs, n, yp, pcs, vp, tp, _stream(stream)), "prop_reconstruct_batch")
+    return Vs, ([t[:q.iters] for t, q in zip(traces, params)] if trace else None)
 
 
 def prop_tv_grad_static(V: torch.Tensor, tv_xy: float, tv_t: float, tv_eps: float, grad: torch.Tensor,

@@ -214,6 +214,42 @@ prop_status reconstruct_impl(Plan& p, const float2* y, const prop_recon_params* 
 
 }  // namespace
 
+bool batch_compatible(const Plan& a, const Plan& b) {
+  return a.nchunks == 1 && b.nchunks == 1 && a.n == b.n && a.cs == b.cs && a.W == b.W && a.device == b.device;
+}
+
+prop_status batch_step(BatchMember* mb, int count, cudaStream_t s) {
+  if (count < 1 || count > kMaxBatch) return fail(PROP_ERR_INVALID_ARG, "batch: 1 to 8 problems");
+  Plan* ps[kMaxBatch];
+  const float2* ym[kMaxBatch];
+  BatchIter it[kMaxBatch];
+  for (int r = 0; r < count; ++r) {
+    Plan& p = *mb[r].p;
+    if (!batch_compatible(p, *mb[0].p)) return fail(PROP_ERR_INVALID_ARG, "batch: plans differ in 2N, bin stride or width");
+    if (mb[r].k == 1) {
+      const size_t vbytes = p.vol_elems() * sizeof(float2);
+      PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));
+      PROP_CUDA(cudaMemsetAsync(p.adam_v, 0, vbytes, s));
+    }
+    p.rows_of = nullptr;
+    if (!mb[r].rows_ready) PROP_LAUNCH(fft_forward_rows(p, mb[r].Vin, 0, s));
+    ps[r] = &p;
+    ym[r] = mb[r].y;
+    it[r].p = &p;
+    it[r].Vin = mb[r].Vin;
+    it[r].Vout = mb[r].Vout;
+    it[r].aa = adam_args(mb[r].q, mb[r].k);
+    it[r].loss_out = mb[r].loss_dst;
+    it[r].fwd_tail = mb[r].next_rows;
+  }
+  PROP_LAUNCH(fft_forward_cols_batch(ps, count, s));
+  PROP_LAUNCH(interp_residual_batch(ps, ym, count, s));
+  PROP_LAUNCH(spread_batch(ps, count, s));
+  PROP_LAUNCH(fft_adjoint_cols_batch(ps, count, s));
+  PROP_LAUNCH(fused_rows_update_batch(it, count, s));
+  return PROP_OK;
+}
+
 prop_status loss_grad_device(Plan& p, const float2* y, const AdamArgs& a, const float2* V, float2* grad,
                              double* loss_out, cudaStream_t s) {
   prop_status st;
@@ -381,6 +417,72 @@ prop_status prop_shard_update(prop_plan plan, const void* y_dev, const void* y_s
   StageScope sc(p, kStOpt, s);
   PROP_LAUNCH(tv_adam(p, (const float2*)V_in_dev, p.grad, p.adam_m, p.adam_v, (float2*)V_out_dev, aa, &p.red_tv,
                       zero, parts + 1, s));
+  return PROP_OK;
+}
+
+prop_status prop_reconstruct_batch(const prop_plan* plans, int count, const void* const* y_dev,
+                                   const prop_recon_params* params, void* const* V_dev, double* const* loss_trace_host,
+                                   void* stream) {
+  if (!plans || !y_dev || !params || !V_dev) return fail(PROP_ERR_INVALID_ARG, "reconstruct_batch: null argument");
+  if (count < 1 || count > kMaxBatch) return fail(PROP_ERR_INVALID_ARG, "reconstruct_batch: count must be 1 to 8");
+  int kmax = 0;
+  for (int r = 0; r < count; ++r) {
+    if (!plans[r] || !y_dev[r] || !V_dev[r]) return fail(PROP_ERR_INVALID_ARG, "reconstruct_batch: null argument");
+    if (!aligned16(V_dev[r]) || !aligned16(y_dev[r]))
+      return fail(PROP_ERR_INVALID_ARG, "reconstruct_batch: buffers must be 16-byte aligned");
+    prop_status st = check_params(&params[r]);
+    if (st != PROP_OK) return st;
+    for (int q = 0; q < r; ++q)
+      if (plans[q] == plans[r]) return fail(PROP_ERR_INVALID_ARG, "reconstruct_batch: a plan appears twice");
+    if (!batch_compatible(*plans[r]->p, *plans[0]->p))
+      return fail(PROP_ERR_INVALID_ARG,
+                  "reconstruct_batch: the plans must share 2N, bin stride, kernel width and device, one bin chunk each");
+    kmax = std::max(kmax, params[r].iters);
+  }
+  Plan& p0 = *plans[0]->p;
+  DeviceGuard g(p0.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* cur[kMaxBatch];
+  float2* nxt[kMaxBatch];
+  for (int r = 0; r < count; ++r) {
+    prop_status st = plan_ensure_recon(plans[r]->p, std::max(params[r].iters, 1));
+    if (st != PROP_OK) return st;
+    cur[r] = (float2*)V_dev[r];
+    nxt[r] = plans[r]->p->vol2;
+  }
+  for (int k = 1; k <= kmax; ++k) {
+    BatchMember mb[kMaxBatch];
+    int n = 0;
+    for (int r = 0; r < count; ++r) {
+      if (k > params[r].iters) continue;
+      Plan& p = *plans[r]->p;
+      mb[n] = BatchMember{&p, (const float2*)y_dev[r], &params[r], k, cur[r], nxt[r], p.loss_dev + (k - 1), k > 1,
+                          k < params[r].iters};
+      ++n;
+    }
+    prop_status st = batch_step(mb, n, s);
+    if (st != PROP_OK) return st;
+    for (int r = 0; r < count; ++r)
+      if (k <= params[r].iters) std::swap(cur[r], nxt[r]);
+  }
+  bool sync = false;
+  for (int r = 0; r < count; ++r) {
+    Plan& p = *plans[r]->p;
+    if (cur[r] != (float2*)V_dev[r])
+      PROP_CUDA(cudaMemcpyAsync(V_dev[r], cur[r], p.vol_elems() * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (loss_trace_host && loss_trace_host[r] && params[r].iters > 0) {
+      PROP_CUDA(cudaMemcpyAsync(loss_trace_host[r], p.loss_dev, sizeof(double) * params[r].iters,
+                                cudaMemcpyDeviceToHost, s));
+      sync = true;
+    }
+  }
+  if (sync) {
+    PROP_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < count; ++r) {
+      prop_status st = check_device_status(*plans[r]->p);
+      if (st != PROP_OK) return st;
+    }
+  }
   return PROP_OK;
 }
 

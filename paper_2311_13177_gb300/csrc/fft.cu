@@ -516,6 +516,14 @@ struct FusedArgs {
   int bh, nbox;        // tensor-copy box height and boxes per unit
 };
 
+// Kernel parameter of the fused row kernel over a batch of problems.
+struct MultiFused {
+  FusedArgs a[kMaxBatch];
+  int fwd_tail[kMaxBatch];
+  int nreq;
+  int unit_begin[kMaxBatch + 1];   // unit (block) ranges of the problems
+};
+
 // Adjoint output into the CTA's gradient buffer gb[i1][col].
 struct OutGrad {
   float2* gb;
@@ -648,15 +656,16 @@ constexpr int fused_min_blocks() {
              : 65536 / (Shape<NFFT, kValsFused<NFFT>>::THREADS * 64);
 }
 
+// The fused row kernel's work on one (image row, 16-bin group) unit: bin
+// group bx of image row `row` (t N + i2); vb, nblk: the unit's index and the
+// unit count of the loss reduction.
 template <int NFFT, bool FWD_TAIL>
-__global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_min_blocks<NFFT>())
-    fused_rows_kernel(FusedArgs a) {
+__device__ __forceinline__ void fused_rows_body(const FusedArgs& a, int bx, size_t row, unsigned vb, unsigned nblk) {
   constexpr int EV = kValsFused<NFFT>;
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
   float2* gb = tw + Shape<NFFT, EV>::TW;  // [N][kFftCols]
-  const size_t row = blockIdx.y;  // t*N + i2
   const int i2 = (int)(row % a.N);
   const int t = (int)(row / a.N);
   build_twiddles<NFFT>(tw, a.twiddle);
@@ -667,7 +676,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
-  const int fbase = blockIdx.x * kFftCols;
+  const int fbase = bx * kFftCols;
   {
     InAdjRows in{a.rows, a.n, a.C, a.Nf, fbase, row};
     OutGrad out{gb, a.deapod, a.N, a.n, a.deapod[i2] * a.scale};
@@ -681,12 +690,49 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_
     OutFwdRows out{a.rows, a.n, a.C, fbase, row};
     fft_pass<NFFT, EV, -1, 0, 1, true, false>(X, tw, col, tl, in, out);
   }
-  finish_loss(local, a.partials, a.counter, a.data_loss, a.loss_out);
+  finish_loss_v(local, a.partials, a.counter, a.data_loss, a.loss_out, vb, nblk);
+}
+
+template <int NFFT, bool FWD_TAIL>
+__global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_min_blocks<NFFT>())
+    fused_rows_kernel(FusedArgs a) {
+  fused_rows_body<NFFT, FWD_TAIL>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x,
+                                  gridDim.x * gridDim.y);
+}
+
+// One launch of the fused row kernel for several problems of the same
+// transform length (a batch of requests): block b serves problem r with
+// unit_begin[r] <= b < unit_begin[r + 1], unit u = b - unit_begin[r] =
+// (image row) nfb + bin group, the same unit and loss-partial order as the
+// problem's own launch, so every result is the same bit for bit.
+template <int NFFT>
+__global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS, fused_min_blocks<NFFT>())
+    fused_rows_multi_kernel(const __grid_constant__ MultiFused m) {
+  int r = 0;
+  while (r + 1 < m.nreq && (int)blockIdx.x >= m.unit_begin[r + 1]) ++r;
+  const unsigned u = blockIdx.x - (unsigned)m.unit_begin[r];
+  const unsigned nu = (unsigned)(m.unit_begin[r + 1] - m.unit_begin[r]);
+  const FusedArgs& a = m.a[r];
+  const int bx = (int)(u % (unsigned)a.nfb);
+  const size_t row = u / (unsigned)a.nfb;
+  if (m.fwd_tail[r])
+    fused_rows_body<NFFT, true>(a, bx, row, u, nu);
+  else
+    fused_rows_body<NFFT, false>(a, bx, row, u, nu);
 }
 
 template <int NFFT>
 size_t fused_smem(int N) {
   return Shape<NFFT, kValsFused<NFFT>>::SMEM + (size_t)N * kFftCols * sizeof(float2);
+}
+
+template <int NFFT>
+cudaError_t launch_fused_multi(const MultiFused& m, cudaStream_t s) {
+  const size_t smem = fused_smem<NFFT>(m.a[0].N);
+  for (int r = 1; r < m.nreq; ++r)
+    if (m.a[r].N != m.a[0].N) return cudaErrorInvalidValue;
+  return launch_dep(fused_rows_multi_kernel<NFFT>, dim3((unsigned)m.unit_begin[m.nreq]),
+                    dim3(Shape<NFFT, kValsFused<NFFT>>::THREADS), smem, s, m);
 }
 
 template <int NFFT>
@@ -882,6 +928,14 @@ struct ColArgs {
   int N, n, qtiles, ntiles, bh, nbox;
 };
 
+// Kernel parameter of a column pass over a batch of problems.
+struct MultiCols {
+  CUtensorMap tm[kMaxBatch];       // each problem's input tensor map
+  ColArgs a[kMaxBatch];
+  int nreq;
+  int cta_begin[kMaxBatch + 1];    // CTA ranges of the problems
+};
+
 template <int NFFT, int KIND>
 constexpr int col_rows() {
   return KIND == kFwdCols ? NFFT / 2 : NFFT;
@@ -904,9 +958,11 @@ constexpr size_t col_smem() {
          Shape<NFFT, kValsPlain<NFFT>>::SMEM + 2 * sizeof(uint64_t);
 }
 
+// The column pass of one problem run by vg persistent CTAs, this being the
+// vb-th: tile vb, vb + vg, ... ; tin is the problem's input tensor map (in
+// the kernel's parameter space).
 template <int NFFT, int KIND>
-__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ctas_per_sm<KIND>())
-    fft_cols_tma_kernel(const __grid_constant__ CUtensorMap tin, ColArgs a) {
+__device__ __forceinline__ void cols_body(const CUtensorMap* tin, const ColArgs& a, int vb, int vg) {
   constexpr int EV = kValsPlain<NFFT>;
   constexpr int H = col_rows<NFFT, KIND>();
   constexpr int NB = col_bufs<KIND>();
@@ -921,7 +977,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ct
     const int t = tile / a.qtiles, qt = tile - (tile / a.qtiles) * a.qtiles;
     mbar_expect_tx(&full[b], tile_bytes);
     for (int i = 0; i < a.nbox; ++i)
-      tma_load_3d(tiles + ((size_t)b * H + (size_t)i * a.bh) * kFftCols, &tin, qt * 2 * kFftCols, i * a.bh, t,
+      tma_load_3d(tiles + ((size_t)b * H + (size_t)i * a.bh) * kFftCols, tin, qt * 2 * kFftCols, i * a.bh, t,
                   &full[b]);
   };
   if (threadIdx.x == 0) {
@@ -934,19 +990,19 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ct
   grid_dep_release();
   if (threadIdx.x == 0)
     for (int b = 0; b < NB; ++b)
-      if ((int)(blockIdx.x + b * gridDim.x) < a.ntiles) issue(blockIdx.x + b * gridDim.x, b);
+      if (vb + b * vg < a.ntiles) issue(vb + b * vg, b);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
   int k = 0;
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
+  for (int tile = vb; tile < a.ntiles; tile += vg, ++k) {
     const int b = k % NB;
     if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NB) & 1))) s_abort = 1;
     __syncthreads();  // the previous tile's last pass is done with X; all threads see s_abort
     if (s_abort) break;
     const size_t t = (size_t)(tile / a.qtiles);
     const size_t q = (size_t)(tile - (tile / a.qtiles) * a.qtiles) * kFftCols;
-    const int next = tile + NB * (int)gridDim.x;
+    const int next = tile + NB * vg;
     auto hook = [&]() {
       if (threadIdx.x == 0 && next < a.ntiles) {
         fence_proxy_async_smem();
@@ -966,8 +1022,26 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ct
     atomicExch(a.err, 1);
     // let copies this CTA issued and nobody consumed land (bounded)
     for (int kk = k; kk < k + NB; ++kk)
-      if ((int)(blockIdx.x + kk * gridDim.x) < a.ntiles) mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
+      if (vb + kk * vg < a.ntiles) mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
   }
+}
+
+template <int NFFT, int KIND>
+__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ctas_per_sm<KIND>())
+    fft_cols_tma_kernel(const __grid_constant__ CUtensorMap tin, ColArgs a) {
+  cols_body<NFFT, KIND>(&tin, a, blockIdx.x, gridDim.x);
+}
+
+// One launch of a column pass for several problems of the same transform
+// length: CTA b serves problem r with cta_begin[r] <= b < cta_begin[r + 1],
+// as CTA b - cta_begin[r] of cta_begin[r + 1] - cta_begin[r].  Every tile is
+// transformed exactly as by the problem's own launch.
+template <int NFFT, int KIND>
+__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ctas_per_sm<KIND>())
+    fft_cols_multi_kernel(const __grid_constant__ MultiCols m) {
+  int r = 0;
+  while (r + 1 < m.nreq && (int)blockIdx.x >= m.cta_begin[r + 1]) ++r;
+  cols_body<NFFT, KIND>(&m.tm[r], m.a[r], (int)blockIdx.x - m.cta_begin[r], m.cta_begin[r + 1] - m.cta_begin[r]);
 }
 
 template <int NFFT>
@@ -994,15 +1068,25 @@ cudaError_t configure_n() {
   int optin = 0, dev = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
-  if (col_smem<NFFT, kFwdCols>() <= (size_t)optin - 1024)
+  if (col_smem<NFFT, kFwdCols>() <= (size_t)optin - 1024) {
     if ((e = cudaFuncSetAttribute(fft_cols_tma_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)col_smem<NFFT, kFwdCols>())))
       return e;
-  if (col_smem<NFFT, kAdjCols>() <= (size_t)optin - 1024)
+    if ((e = cudaFuncSetAttribute(fft_cols_multi_kernel<NFFT, kFwdCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<NFFT, kFwdCols>())))
+      return e;
+  }
+  if (col_smem<NFFT, kAdjCols>() <= (size_t)optin - 1024) {
     if ((e = cudaFuncSetAttribute(fft_cols_tma_kernel<NFFT, kAdjCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)col_smem<NFFT, kAdjCols>())))
       return e;
+    if ((e = cudaFuncSetAttribute(fft_cols_multi_kernel<NFFT, kAdjCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem<NFFT, kAdjCols>())))
+      return e;
+  }
   const int fsm = (int)fused_smem<NFFT>(NFFT / 2);
+  if ((e = cudaFuncSetAttribute(fused_rows_multi_kernel<NFFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
+    return e;
   if ((e = cudaFuncSetAttribute(fused_rows_kernel<NFFT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
     return e;
   if ((e = cudaFuncSetAttribute(fused_rows_kernel<NFFT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm)))
@@ -1057,6 +1141,34 @@ cudaError_t dispatch_cols_tma(int n, int kind, const CUtensorMap& tm, const ColA
   switch (n) {
 #define CASE(v) \
   case v: return launch_cols_tma<v>(kind, tm, a, sms, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int NFFT>
+cudaError_t launch_cols_multi(int kind, const MultiCols& m, int ctas, cudaStream_t s) {
+  const dim3 grid((unsigned)ctas), block(Shape<NFFT, kValsPlain<NFFT>>::THREADS);
+  if (kind == kFwdCols)
+    return launch_dep(fft_cols_multi_kernel<NFFT, kFwdCols>, grid, block, col_smem<NFFT, kFwdCols>(), s, m);
+  return launch_dep(fft_cols_multi_kernel<NFFT, kAdjCols>, grid, block, col_smem<NFFT, kAdjCols>(), s, m);
+}
+
+cudaError_t dispatch_cols_multi(int n, int kind, const MultiCols& m, int ctas, cudaStream_t s) {
+  switch (n) {
+#define CASE(v) \
+  case v: return launch_cols_multi<v>(kind, m, ctas, s);
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch_fused_multi(int n, const MultiFused& m, cudaStream_t s) {
+  switch (n) {
+#define CASE(v) \
+  case v: return launch_fused_multi<v>(m, s);
     PROP_FFT_SIZES(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -1387,6 +1499,97 @@ cudaError_t fft_adjoint_rows(const Plan& p, float2* out, int f0, float scale, cu
   a.Cv = std::min(p.chunk, p.Nf - f0);
   dim3 grid((a.Cv + kFftCols - 1) / kFftCols, p.T * p.N);
   return dispatch(p.n, kAdjRows, a, grid, s);
+}
+
+namespace {
+FusedArgs fused_args(const Plan& p, const float2* Vin, float2* m, float2* v, float2* Vout, const AdamArgs& aa,
+                     const Reducer* red, const double* data_loss, double* loss_out) {
+  FusedArgs a{};
+  a.rows = p.rows;
+  a.deapod = p.deapod;
+  a.twiddle = p.twiddle;
+  a.Vin = Vin;
+  a.Vout = Vout;
+  a.m = m;
+  a.v = v;
+  a.partials = red->partials;
+  a.counter = red->counter;
+  a.data_loss = data_loss;
+  a.loss_out = loss_out;
+  a.N = p.N;
+  a.n = p.n;
+  a.Nf = p.Nf;
+  a.C = p.cs;
+  a.T = p.T;
+  a.scale = 1.0f / (float)p.N;
+  a.ad = aa;
+  a.err = p.status_dev;
+  a.nfb = (p.Nf + kFftCols - 1) / kFftCols;
+  a.units = a.nfb * p.T * p.N;
+  return a;
+}
+
+// Column pass over a batch: CTAs split by tile count.
+cudaError_t cols_batch(Plan* const* ps, int count, int kind, cudaStream_t s) {
+  if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
+  bool tma = true;
+  for (int r = 0; r < count; ++r) {
+    tma = tma && (kind == kFwdCols ? ps[r]->cols_tma_fwd : ps[r]->cols_tma_adj);
+    if (ps[r]->n != ps[0]->n) return cudaErrorInvalidValue;
+  }
+  if (!tma) {  // untiled fallback: one launch per plan
+    for (int r = 0; r < count; ++r) {
+      const cudaError_t e = kind == kFwdCols ? fft_forward_cols(*ps[r], s) : fft_adjoint_cols(*ps[r], s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  MultiCols m{};
+  m.nreq = count;
+  long work[kMaxBatch];
+  int cap[kMaxBatch];
+  for (int r = 0; r < count; ++r) {
+    m.tm[r] = kind == kFwdCols ? ps[r]->tm_rows : ps[r]->tm_grid;
+    m.a[r] = col_args(*ps[r], kind);
+    work[r] = m.a[r].ntiles;
+    cap[r] = std::max(1, m.a[r].ntiles);
+  }
+  const int per_sm = kind == kFwdCols ? col_ctas_per_sm<kFwdCols>() : col_ctas_per_sm<kAdjCols>();
+  const int ctas = split_ctas(work, cap, count, std::max(count, per_sm * ps[0]->num_sms), m.cta_begin);
+  return dispatch_cols_multi(ps[0]->n, kind, m, ctas, s);
+}
+}  // namespace
+
+cudaError_t fft_forward_cols_batch(Plan* const* ps, int count, cudaStream_t s) {
+  return cols_batch(ps, count, kFwdCols, s);
+}
+cudaError_t fft_adjoint_cols_batch(Plan* const* ps, int count, cudaStream_t s) {
+  return cols_batch(ps, count, kAdjCols, s);
+}
+
+cudaError_t fused_rows_update_batch(const BatchIter* it, int count, cudaStream_t s) {
+  if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
+  MultiFused m{};
+  m.nreq = 0;
+  m.unit_begin[0] = 0;
+  for (int r = 0; r < count; ++r) {
+    const Plan& p = *it[r].p;
+    if (p.nchunks != 1 || p.n != it[0].p->n) return cudaErrorInvalidValue;
+    if (p.fused_ws) {  // the persistent warp-specialised kernel runs on its own
+      const cudaError_t e = fused_rows_update(p, it[r].Vin, p.adam_m, p.adam_v, it[r].Vout, it[r].aa, &p.red_tv,
+                                              p.scalars, it[r].loss_out, it[r].fwd_tail, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    const int q = m.nreq++;
+    m.a[q] = fused_args(p, it[r].Vin, p.adam_m, p.adam_v, it[r].Vout, it[r].aa, &p.red_tv, p.scalars,
+                        it[r].loss_out);
+    if (m.a[q].units > p.red_tv.capacity) return cudaErrorInvalidValue;
+    m.fwd_tail[q] = it[r].fwd_tail ? 1 : 0;
+    m.unit_begin[q + 1] = m.unit_begin[q] + m.a[q].units;
+  }
+  if (m.nreq == 0) return cudaSuccess;
+  return dispatch_fused_multi(it[0].p->n, m, s);
 }
 
 cudaError_t fused_rows_update(const Plan& p, const float2* Vin, float2* m, float2* v, float2* Vout,

@@ -75,28 +75,33 @@ __device__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// Deterministic grid reduction: each block's partial, summed by the last block.
-__device__ void reduce_to(double local, double* partials, unsigned int* counter, double* out) {
+// Deterministic grid reduction: each block's partial, summed by the last
+// block; vb, nblk: this block's index and the block count of the reduction.
+__device__ void reduce_to_v(double local, double* partials, unsigned int* counter, double* out, unsigned vb,
+                            unsigned nblk) {
   __shared__ double sh[32];
   __shared__ bool last;
   const double bs = block_sum(local, sh);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bs;
+    partials[vb] = bs;
     __threadfence();
     const unsigned prev = atomicAdd(counter, 1u);
-    last = prev == gridDim.x - 1;
+    last = prev == nblk - 1;
   }
   __syncthreads();
   if (last) {
     __threadfence();
     double s = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&partials[i]);
+    for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) s += __ldcg(&partials[i]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
       *out = s;
       *counter = 0u;
     }
   }
+}
+__device__ void reduce_to(double local, double* partials, unsigned int* counter, double* out) {
+  reduce_to_v(local, partials, counter, out, blockIdx.x, gridDim.x);
 }
 
 struct ItemGeom {
@@ -317,8 +322,10 @@ constexpr int kInterp2Threads = 32 * (kInterpConsumers + 1);  // plus one produc
 // loads), and 64 / CS samples per warp and round.  The metadata of an item
 // (sample index, packed first tap, the 2W weights) is fetched before its
 // tile is awaited, one sample per lane, and handed out by shuffles.
+// The work of one persistent CTA: items [it_beg, it_end); vb, vg: the CTA's
+// index and the CTA count of the |r|^2 reduction.
 template <int CS, int W>
-__global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs a) {
+__device__ __forceinline__ void interp2_body(const InterpArgs& a, int it_beg, int it_end, unsigned vb, unsigned vg) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int NCW = kInterpConsumers;
   constexpr int LPS = CS / 2;   // lanes per sample
@@ -353,8 +360,7 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
   if (warp == NCW) {
     if (lane == 0) {
       int k = 0;
-      const int it_end = a.cta_off[blockIdx.x + 1];
-      for (int item = a.cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
+      for (int item = it_beg; item < it_end; ++item, ++k) {
         const int b = k % a.nbuf;
         if (k >= a.nbuf && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / a.nbuf) - 1) & 1))) {
           s_abort = 1;
@@ -371,8 +377,7 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
     const int f_lo = 2 * sub;
     const bool b0 = f_lo < a.Cv, b1 = f_lo + 1 < a.Cv;
     int k = 0;
-    const int it_end = a.cta_off[blockIdx.x + 1];
-    for (int item = a.cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
+    for (int item = it_beg; item < it_end; ++item, ++k) {
       const int b = k % a.nbuf;
       const ItemGeom g = item_geom(a, item);
       // lane L prefetches the warp's sample of round L / SPW, slot L % SPW
@@ -476,7 +481,35 @@ __global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs 
   }
   __syncthreads();
   if (s_abort && threadIdx.x == 0) atomicExch(a.err, 1);
-  if (a.partials) reduce_to((double)sumsq, a.partials, a.counter, a.sumsq_out);
+  if (a.partials) reduce_to_v((double)sumsq, a.partials, a.counter, a.sumsq_out, vb, vg);
+}
+
+template <int CS, int W>
+__global__ void __launch_bounds__(kInterp2Threads, 1) interp2_kernel(InterpArgs a) {
+  interp2_body<CS, W>(a, a.cta_off[blockIdx.x], a.cta_off[blockIdx.x + 1], blockIdx.x, gridDim.x);
+}
+
+// Kernel parameter of the interpolation over a batch of problems.
+struct MultiInterp {
+  InterpArgs a[kMaxBatch];
+  int plan_ctas[kMaxBatch];      // CTAs each problem's items were balanced over
+  int nreq;
+  int cta_begin[kMaxBatch + 1];  // CTA ranges of the problems
+};
+
+// One launch for several problems with the same bin stride and kernel
+// width: CTA b serves problem r (cta_begin[r] <= b < cta_begin[r + 1]) as
+// its CTA v of c = cta_begin[r + 1] - cta_begin[r] and takes the items the
+// problem's plan balanced over its CTAs v P / c .. (v + 1) P / c - 1, so every
+// sample is computed as in the problem's own launch.
+template <int CS, int W>
+__global__ void __launch_bounds__(kInterp2Threads, 1) interp2_multi_kernel(const __grid_constant__ MultiInterp m) {
+  int r = 0;
+  while (r + 1 < m.nreq && (int)blockIdx.x >= m.cta_begin[r + 1]) ++r;
+  const int v = (int)blockIdx.x - m.cta_begin[r], c = m.cta_begin[r + 1] - m.cta_begin[r];
+  const int P = m.plan_ctas[r];
+  const InterpArgs& a = m.a[r];
+  interp2_body<CS, W>(a, a.cta_off[(long)v * P / c], a.cta_off[(long)(v + 1) * P / c], (unsigned)v, (unsigned)c);
 }
 
 // contrib[m][f] = conj(P[j_m][f0 + f]) r_m, LP lanes per sample.
@@ -675,10 +708,10 @@ constexpr int kSpreadThreads = 32 * (kSpreadConsumers + 1);   // plus one produc
 // used it, so the lists come from shared memory and only the phased-residual
 // rows (mostly L1/L2 hits) are read from global memory.  Used when every
 // item fits a stage (the plan checks).
+// The work of one persistent CTA on items [it_beg, it_end).
 template <int CS, bool GROUPED>
-__global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
-    spread_stage_kernel(float2* grid, const float2* contrib, const int4* sitems, const int2* blob,
-                        const int* cta_off, int Cv, int n, int* err) {
+__device__ __forceinline__ void spread_stage_body(float2* grid, const float2* contrib, const int4* sitems,
+                                                  const int2* blob, int it_beg, int it_end, int Cv, int n, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int NCW = kSpreadConsumers;
   constexpr int NBUF = 2;
@@ -705,8 +738,7 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
     grid_dep_release();
     if (lane == 0) {
       int k = 0;
-      const int it_end = cta_off[blockIdx.x + 1];
-      for (int item = cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
+      for (int item = it_beg; item < it_end; ++item, ++k) {
         const int b = k % NBUF;
         if (k >= NBUF && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / NBUF) - 1) & 1))) {
           s_abort = 1;
@@ -726,8 +758,7 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
     grid_dep_wait();
     grid_dep_release();
     int k = 0;
-    const int it_end = cta_off[blockIdx.x + 1];
-    for (int item = cta_off[blockIdx.x]; item < it_end; ++item, ++k) {
+    for (int item = it_beg; item < it_end; ++item, ++k) {
       const int b = k % NBUF;
       const int4 d = __ldg(&sitems[item]);
       const int ncp = (d.y + 1) & ~1;
@@ -743,6 +774,45 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
   }
   __syncthreads();
   if (s_abort && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+template <int CS, bool GROUPED>
+__global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
+    spread_stage_kernel(float2* grid, const float2* contrib, const int4* sitems, const int2* blob,
+                        const int* cta_off, int Cv, int n, int* err) {
+  spread_stage_body<CS, GROUPED>(grid, contrib, sitems, blob, cta_off[blockIdx.x], cta_off[blockIdx.x + 1], Cv, n,
+                                 err);
+}
+
+// Kernel parameter of the staged spread over a batch of problems.
+struct SpreadArgs {
+  float2* grid;
+  const float2* contrib;
+  const int4* sitems;
+  const int2* blob;
+  const int* cta_off;
+  int Cv, n, plan_ctas;
+  int* err;
+};
+struct MultiSpread {
+  SpreadArgs a[kMaxBatch];
+  int nreq;
+  int cta_begin[kMaxBatch + 1];
+};
+
+// One launch for several problems with the same bin stride and list kind,
+// CTAs mapped onto each problem's balanced item ranges as in
+// interp2_multi_kernel; every cell sums its own terms in its list's order.
+template <int CS, bool GROUPED>
+__global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
+    spread_stage_multi_kernel(const __grid_constant__ MultiSpread m) {
+  int r = 0;
+  while (r + 1 < m.nreq && (int)blockIdx.x >= m.cta_begin[r + 1]) ++r;
+  const int v = (int)blockIdx.x - m.cta_begin[r], c = m.cta_begin[r + 1] - m.cta_begin[r];
+  const SpreadArgs& a = m.a[r];
+  const int P = a.plan_ctas;
+  spread_stage_body<CS, GROUPED>(a.grid, a.contrib, a.sitems, a.blob, a.cta_off[(long)v * P / c],
+                                 a.cta_off[(long)(v + 1) * P / c], a.Cv, a.n, a.err);
 }
 
 // Runtime bin stride (any C <= 2 LP): LP lanes per cell, bins sub and
@@ -848,6 +918,10 @@ cudaError_t allow_smem(K kernel, int optin) {
 template <int W>
 cudaError_t configure_interp(int optin) {
   cudaError_t e;
+  if ((e = allow_smem(interp2_multi_kernel<32, W>, optin))) return e;
+  if ((e = allow_smem(interp2_multi_kernel<64, W>, optin))) return e;
+  if ((e = allow_smem(interp2_multi_kernel<16, W>, optin))) return e;
+  if ((e = allow_smem(interp2_multi_kernel<8, W>, optin))) return e;
   if ((e = allow_smem(interp2_kernel<32, W>, optin))) return e;
   if ((e = allow_smem(interp2_kernel<64, W>, optin))) return e;
   if ((e = allow_smem(interp2_kernel<16, W>, optin))) return e;
@@ -871,6 +945,10 @@ cudaError_t nufft_configure(int smem_optin) {
   if ((e = cudaFuncSetAttribute(spread_stage_kernel<CSV, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
   SA(8, false) SA(16, false) SA(32, false) SA(64, false) SA(8, true) SA(16, true) SA(32, true) SA(64, true)
 #undef SA
+#define SA(CSV, GR) \
+  if ((e = cudaFuncSetAttribute(spread_stage_multi_kernel<CSV, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
+  SA(8, false) SA(16, false) SA(32, false) SA(64, false) SA(8, true) SA(16, true) SA(32, true) SA(64, true)
+#undef SA
   return cudaSuccess;
 }
 
@@ -879,6 +957,48 @@ int interp_buffers(const Plan& p) {
   const size_t tile = (size_t)HW * HW * p.cs * sizeof(float2);
   // two buffers when they fit next to the barriers and the static shared memory
   return 2 * tile + 1024 <= (size_t)p.smem_optin ? 2 : 1;
+}
+
+InterpArgs interp_args(const Plan& p, int f0, int nbins, float2* y, const float2* y_meas, bool accumulate,
+                       const Reducer* red, double* sumsq, float2* contrib) {
+  InterpArgs a{};
+  a.grid = p.grid;
+  a.kb_idx = p.kb_idx;
+  a.kb_w = p.kb_w;
+  a.order = p.order;
+  a.items = p.items;
+  a.phase = p.phase;
+  a.y = y;
+  a.y_meas = y_meas;
+  a.contrib = contrib;
+  a.partials = red ? red->partials : nullptr;
+  a.counter = red ? red->counter : nullptr;
+  a.sumsq_out = sumsq;
+  a.err = p.status_dev;
+  a.n_items = p.n_items;
+  a.R = p.R;
+  a.n = p.n;
+  a.C = p.cs;
+  a.Cv = nbins;
+  a.f0 = f0;
+  a.Nf = p.Nf;
+  a.scale = 1.0f / (float)p.N;
+  a.accumulate = accumulate ? 1 : 0;
+  a.TI = p.interp_tile;
+  a.tps = p.n / p.interp_tile;
+  a.nbuf = interp_buffers(p);
+  a.cta_off = p.item_cta_off;
+  return a;
+}
+
+template <int W>
+cudaError_t launch_interp_multi(int cs, const MultiInterp& m, int ctas, size_t smem, cudaStream_t s) {
+  const dim3 grid((unsigned)ctas), block(kInterp2Threads);
+  if (cs == 32) return launch_dep(interp2_multi_kernel<32, W>, grid, block, smem, s, m);
+  if (cs == 64) return launch_dep(interp2_multi_kernel<64, W>, grid, block, smem, s, m);
+  if (cs == 16) return launch_dep(interp2_multi_kernel<16, W>, grid, block, smem, s, m);
+  if (cs == 8) return launch_dep(interp2_multi_kernel<8, W>, grid, block, smem, s, m);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_meas, bool accumulate,
@@ -921,6 +1041,98 @@ cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_
   const int lp = lanes_for(nbins);
   dim3 grid((unsigned)blocks);
   return p.W == 8 ? launch_interp<8>(lp, p.cs, a, grid, smem, s) : launch_interp<6>(lp, p.cs, a, grid, smem, s);
+}
+
+cudaError_t interp_residual_batch(Plan* const* ps, const float2* const* y_meas, int count, cudaStream_t s) {
+  if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
+  MultiInterp m{};
+  m.nreq = 0;
+  Plan* mp[kMaxBatch];
+  for (int r = 0; r < count; ++r) {
+    Plan& p = *ps[r];
+    if (p.nchunks != 1) return cudaErrorInvalidValue;
+    const bool multi = interp2_eligible(p.cs, p.Nf) && p.cs == ps[0]->cs && p.W == ps[0]->W &&
+                       interp_buffers(p) == interp_buffers(*ps[0]) && p.n_items > 0;
+    if (!multi) {  // its own launch
+      const cudaError_t e = interp(p, 0, p.Nf, p.resid, y_meas[r], false, &p.red_interp, p.scalars, p.contrib, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    mp[m.nreq] = &p;
+    m.a[m.nreq] = interp_args(p, 0, p.Nf, p.resid, y_meas[r], false, &p.red_interp, p.scalars, p.contrib);
+    m.plan_ctas[m.nreq] = p.interp_ctas;
+    ++m.nreq;
+  }
+  if (m.nreq == 0) return cudaSuccess;
+  long work[kMaxBatch];
+  int cap[kMaxBatch];
+  for (int r = 0; r < m.nreq; ++r) {
+    work[r] = mp[r]->M;
+    cap[r] = mp[r]->interp_ctas;
+    if (mp[r]->red_interp.capacity < cap[r]) return cudaErrorInvalidValue;
+  }
+  const Plan& p0 = *mp[0];
+  const int ctas = split_ctas(work, cap, m.nreq, std::max(m.nreq, p0.num_sms), m.cta_begin);
+  const int HW = p0.interp_tile + p0.W - 1;
+  const int nbuf = interp_buffers(p0);
+  const size_t smem = (size_t)nbuf * HW * HW * p0.cs * sizeof(float2) + 2 * nbuf * sizeof(uint64_t);
+  return p0.W == 8 ? launch_interp_multi<8>(p0.cs, m, ctas, smem, s) : launch_interp_multi<6>(p0.cs, m, ctas, smem, s);
+}
+
+cudaError_t spread_batch(Plan* const* ps, int count, cudaStream_t s) {
+  if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
+  MultiSpread m{};
+  m.nreq = 0;
+  Plan* mp[kMaxBatch];
+  const auto staged = [](const Plan& p) {
+    return p.spread_grouped || (p.spread_staged && (p.cs == 8 || p.cs == 16 || p.cs == 32 || p.cs == 64));
+  };
+  for (int r = 0; r < count; ++r) {
+    Plan& p = *ps[r];
+    const bool multi = staged(p) && p.cs == ps[0]->cs && p.spread_grouped == ps[0]->spread_grouped &&
+                       staged(*ps[0]) && p.n_sitems > 0;
+    if (!multi) {
+      const cudaError_t e = spread(p, 0, p.Nf, p.resid, true, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    mp[m.nreq] = &p;
+    SpreadArgs& a = m.a[m.nreq];
+    a.grid = p.grid;
+    a.contrib = p.contrib;
+    a.sitems = p.sitems;
+    a.blob = p.sblob;
+    a.cta_off = p.sitem_cta_off;
+    a.Cv = p.Nf;
+    a.n = p.n;
+    a.plan_ctas = p.spread_ctas;
+    a.err = p.status_dev;
+    ++m.nreq;
+  }
+  if (m.nreq == 0) return cudaSuccess;
+  long work[kMaxBatch];
+  int cap[kMaxBatch];
+  for (int r = 0; r < m.nreq; ++r) {
+    work[r] = (long)mp[r]->spread_entries;
+    cap[r] = mp[r]->spread_ctas;
+  }
+  const Plan& p0 = *mp[0];
+  const int ctas = split_ctas(work, cap, m.nreq, std::max(m.nreq, kSpreadCtasPerSm * p0.num_sms), m.cta_begin);
+  const dim3 g((unsigned)ctas), b(kSpreadThreads);
+  const size_t smem = spread_stage_smem();
+#define SM(CSV, GR) return launch_dep(spread_stage_multi_kernel<CSV, GR>, g, b, smem, s, m)
+  if (p0.spread_grouped) {
+    if (p0.cs == 32) SM(32, true);
+    if (p0.cs == 64) SM(64, true);
+    if (p0.cs == 16) SM(16, true);
+    SM(8, true);
+  } else {
+    if (p0.cs == 32) SM(32, false);
+    if (p0.cs == 64) SM(64, false);
+    if (p0.cs == 16) SM(16, false);
+    SM(8, false);
+  }
+#undef SM
 }
 
 cudaError_t residual(const Plan& p, const float2* y_sum, const float2* y_meas, float2* r, bool with_contrib,

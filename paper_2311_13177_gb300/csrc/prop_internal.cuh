@@ -36,6 +36,7 @@ constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 constexpr int interp_tile_for(int cs, int W) { return (void)W, cs <= 32 ? 16 : 8; }
 
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
+constexpr int kMaxBatch = 8;       // most problems in one multi-problem launch
 
 // Status plumbing -----------------------------------------------------------
 void set_error(const std::string& msg);
@@ -330,6 +331,77 @@ cudaError_t render(const Plan& p, const float2* V, int f_lo, int f_hi, float2* i
 // PSNR of |img| against |ref| over `count` complex values: 10 log10(max|ref|^2 / mean (|img| - |ref|)^2)
 // into *out (device); scratch: p.psnr_scratch with p.psnr_cap block partials.
 cudaError_t psnr(const Plan& p, const float2* img, const float2* ref, long count, double* out, cudaStream_t s);
+
+// Multi-problem launches (a batch of plans with the same transform length
+// 2N, bin stride and kernel width, one bin chunk each): one launch per stage
+// serves every plan of the batch; each plan's results are the same bit for
+// bit as from its own launches.
+struct BatchIter {
+  Plan* p;
+  const float2* Vin;    // V_{k-1}
+  float2* Vout;         // V_k
+  AdamArgs aa;          // Adam step k
+  double* loss_out;     // L(V_{k-1})
+  bool fwd_tail;        // leave the forward row transform of V_k in p->rows
+};
+// Splits `total` persistent CTAs over `count` problems in proportion to
+// their work (every problem gets at least one and at most cap[i]);
+// begin[count + 1] receives the CTA ranges; returns the CTAs used.
+inline int split_ctas(const long* work, const int* cap, int count, int total, int* begin) {
+  long sum = 0;
+  for (int i = 0; i < count; ++i) sum += work[i] > 0 ? work[i] : 1;
+  int c[kMaxBatch];
+  int used = 0;
+  for (int i = 0; i < count; ++i) {
+    const long w = work[i] > 0 ? work[i] : 1;
+    c[i] = (int)((w * (long)total) / (sum > 0 ? sum : 1));
+    c[i] = c[i] < 1 ? 1 : (c[i] > cap[i] ? cap[i] : c[i]);
+    used += c[i];
+  }
+  // hand leftover CTAs to the problems with the most work per CTA
+  while (used < total) {
+    int best = -1;
+    double br = 0.0;
+    for (int i = 0; i < count; ++i)
+      if (c[i] < cap[i]) {
+        const double r = (double)(work[i] > 0 ? work[i] : 1) / c[i];
+        if (best < 0 || r > br) {
+          best = i;
+          br = r;
+        }
+      }
+    if (best < 0) break;
+    ++c[best];
+    ++used;
+  }
+  begin[0] = 0;
+  for (int i = 0; i < count; ++i) begin[i + 1] = begin[i] + c[i];
+  return begin[count];
+}
+cudaError_t fft_forward_cols_batch(Plan* const* ps, int count, cudaStream_t s);
+cudaError_t fft_adjoint_cols_batch(Plan* const* ps, int count, cudaStream_t s);
+cudaError_t fused_rows_update_batch(const BatchIter* it, int count, cudaStream_t s);
+// nufft.cu: the residual interpolation (each plan: its own y and measured
+// data, residual into p->resid, phased residual into p->contrib, FP64 |r|^2
+// into p->scalars) and the spread of p->contrib into p->grid.
+cudaError_t interp_residual_batch(Plan* const* ps, const float2* const* y_meas, int count, cudaStream_t s);
+cudaError_t spread_batch(Plan* const* ps, int count, cudaStream_t s);
+// api.cu: one Adam iteration of every member, the stages launched once for
+// the whole batch (members share 2N, bin stride and kernel width and have one
+// bin chunk each; batch_compatible says whether two plans can share).
+struct BatchMember {
+  Plan* p;
+  const float2* y;               // measured data (device)
+  const prop_recon_params* q;
+  int k;                         // iteration (1-based)
+  const float2* Vin;
+  float2* Vout;
+  double* loss_dst;              // device: L(Vin)
+  bool rows_ready;               // p->rows holds the forward row transform of Vin
+  bool next_rows;                // leave the forward row transform of Vout in p->rows
+};
+bool batch_compatible(const Plan& a, const Plan& b);
+prop_status batch_step(BatchMember* mb, int count, cudaStream_t s);
 
 // fft.cu, single bin chunk only: the inverse row FFT of p.rows (the last
 // adjoint pass) fused with TV + Adam (Vin -> Vout, moments m, v) and, with

@@ -2,18 +2,25 @@
 // GPU (the C ABI's prop_serve_* calls).
 //
 // Each request is a full reconstruction problem (geometry, Adam and TV
-// settings, blade data).  A scheduler thread admits queued requests in FIFO
+// settings, blade data).  Admission workers admit queued requests in FIFO
 // order while a slot is free and the request's device footprint fits the
-// server's HBM budget, builds its plan inside one pre-allocated device
-// arena (so retiring a request never synchronises the device), and then
-// keeps every admitted request's non-blocking stream fed with Adam
-// iterations (at most two in flight per request), so the kernels of
-// different requests overlap on the GPU.  A request that finishes has its
-// volume copied back, its arena memory returned, and the next waiting
-// request is admitted at once.  Every request's arithmetic runs in its own
-// buffers with deterministic kernels, so its result is bitwise the same
-// alone or in any mix.  Latency is measured on the host from submission to
-// the completion of the final copy.
+// server's HBM budget, build its plan inside one pre-allocated device arena
+// (so retiring a request never synchronises the device) and upload its data.
+// The scheduler thread groups the running requests by kernel class (the
+// same transform length 2N, bin stride and kernel width: one set of kernel
+// instances) and advances every class with batched iterations: one launch
+// per stage (column FFTs, interpolation, spread, fused row update) serves
+// every request of the class in the batch, each on the CTAs its share of
+// the work earns, at most two batched iterations in flight per class, the
+// classes on their own streams so that they overlap too.  Requests of
+// different blade counts, frame counts and data share a launch; requests
+// join their class's next batched iteration as soon as they are admitted and
+// leave it when they finish.  A finished request has its volume copied back
+// on its own stream, its arena memory returned, and the next waiting request
+// is admitted at once.  Every request's arithmetic runs in its own buffers
+// with the same kernels' per-element work as a lone solve, so its result is
+// bitwise the same alone or in any mix.  Latency is measured on the host from
+// submission to the completion of the final copy.
 #include "prop_internal.cuh"
 
 #include <algorithm>
@@ -25,6 +32,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 
 namespace prop {
 namespace {
@@ -141,7 +149,8 @@ struct Request {
   float2* cur = nullptr;
   float2* nxt = nullptr;
   int k = 0;
-  std::deque<cudaEvent_t> inflight;
+  std::deque<cudaEvent_t> inflight;   // unused with batched iterations (kept empty)
+  cudaEvent_t last_ev = nullptr;      // completes with the last batched iteration this request took part in
   cudaEvent_t done_ev = nullptr;
   bool copying = false;
   float2* pinned = nullptr;
@@ -167,6 +176,13 @@ struct prop_server_s {
   std::deque<prop_ticket> pending;
   std::map<prop_ticket, std::unique_ptr<prop::Request>> reqs;
   std::vector<prop::Request*> active;
+  // kernel classes of the running requests: (2N, bin stride, width) -> stream
+  // and the events of its batched iterations in flight
+  struct Klass {
+    cudaStream_t stream = nullptr;
+    std::deque<cudaEvent_t> inflight;
+  };
+  std::map<std::tuple<int, int, int>, Klass> klasses;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<float2*, size_t>> pinned_pool;
   size_t reserved = 0;  // footprints of admitted requests
@@ -222,6 +238,7 @@ void release(prop_server_s* s, Request* r) {
   r->inflight.clear();
   if (r->done_ev) s->ev_pool.push_back(r->done_ev);
   r->done_ev = nullptr;
+  r->last_ev = nullptr;  // owned by its class's in-flight list
   if (r->alloc) {
     r->alloc->release(r->y_dev);
     r->alloc->release(r->v_dev);
@@ -356,20 +373,33 @@ void admission(prop_server_s* s) {
   }
 }
 
+std::tuple<int, int, int> klass_of(const Plan& p) { return std::make_tuple(p.n, p.cs, p.W); }
+
 void scheduler(prop_server_s* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     if (s->stop && s->active.empty() && s->pending.empty() && s->admitting == 0) break;
-    // Work: keep every active stream fed, retire finished requests.
     bool progressed = false;
+    // completed batched iterations of every class
+    for (auto& kv : s->klasses) {
+      auto& q = kv.second.inflight;
+      while (!q.empty() && cudaEventQuery(q.front()) == cudaSuccess) {
+        for (Request* r : s->active)
+          if (r->last_ev == q.front()) r->last_ev = nullptr;  // its iterations are all done
+        s->ev_pool.push_back(q.front());
+        q.pop_front();
+      }
+    }
+    // retire, cancel, start result copies
     std::vector<Request*> still;
     for (Request* r : s->active) {
-      while (!r->inflight.empty() && cudaEventQuery(r->inflight.front()) == cudaSuccess) {
-        s->ev_pool.push_back(r->inflight.front());
-        r->inflight.pop_front();
-      }
+      const bool idle = !r->last_ev || cudaEventQuery(r->last_ev) == cudaSuccess;
       if (r->cancel) {
+        if (!idle) {
+          still.push_back(r);
+          continue;
+        }
         cudaStreamSynchronize(r->stream);
         release(s, r);
         finish(s, r, kCancelled, PROP_ERR_CANCELLED, "cancelled");
@@ -398,29 +428,9 @@ void scheduler(prop_server_s* s) {
         progressed = true;
         continue;
       }
-      if (r->k < r->params.iters && r->inflight.size() < 2) {
-        Plan& p = *r->plan;
-        const int k = r->k + 1;
-        // consecutive iterations of one request on its own plan: the fused
-        // row kernel hands the next forward row transform along
-        const prop_status st = plan_step(p, r->y_dev, &r->params, k, r->cur, r->nxt, p.loss_dev + (k - 1),
-                                         r->stream, k > 1, k < r->params.iters);
-        if (st != PROP_OK) {
-          const std::string msg = prop_last_error();
-          cudaStreamSynchronize(r->stream);
-          release(s, r);
-          finish(s, r, kFailed, st, msg);
-          s->cv_done.notify_all();
-          progressed = true;
-          continue;
-        }
-        std::swap(r->cur, r->nxt);
-        r->k = k;
-        cudaEvent_t e = take_ev(s);
-        cudaEventRecord(e, r->stream);
-        r->inflight.push_back(e);
-        progressed = true;
-      } else if (r->k >= r->params.iters && r->inflight.empty()) {
+      if (r->k >= r->params.iters) {
+        // the result copy runs on the request's own stream after its last iteration
+        if (r->last_ev) cudaStreamWaitEvent(r->stream, r->last_ev, 0);
         const size_t vb = r->plan->vol_elems() * sizeof(float2);
         cudaMemcpyAsync(r->pinned, r->cur, vb, cudaMemcpyDeviceToHost, r->stream);
         *r->loss_pinned = 0.0;
@@ -435,10 +445,78 @@ void scheduler(prop_server_s* s) {
     }
     if (still.size() != s->active.size()) s->cv_admit.notify_all();
     s->active.swap(still);
+    // one batched iteration for every class with work and fewer than two in flight
+    std::map<std::tuple<int, int, int>, std::vector<Request*>> ready;
+    for (Request* r : s->active)
+      if (!r->cancel && !r->copying && r->k < r->params.iters) ready[klass_of(*r->plan)].push_back(r);
+    for (auto& kv : ready) {
+      prop_server_s::Klass& K = s->klasses[kv.first];
+      if (K.inflight.size() >= 2) continue;
+      if (!K.stream && cudaStreamCreateWithFlags(&K.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        K.stream = nullptr;
+        continue;
+      }
+      std::vector<Request*>& rs = kv.second;
+      // the requests furthest behind first (admission order among equals)
+      std::stable_sort(rs.begin(), rs.end(), [](const Request* a, const Request* b) { return a->k < b->k; });
+      const int n = std::min<int>((int)rs.size(), kMaxBatch);
+      BatchMember mb[kMaxBatch];
+      for (int i = 0; i < n; ++i) {
+        Request* r = rs[i];
+        Plan& p = *r->plan;
+        const int k = r->k + 1;
+        mb[i] = BatchMember{&p, r->y_dev, &r->params, k, r->cur, r->nxt, p.loss_dev + (k - 1), k > 1,
+                            k < r->params.iters};
+        // a request's first batched iteration follows its uploads
+        if (r->k == 0) {
+          cudaEvent_t up = take_ev(s);
+          cudaEventRecord(up, r->stream);
+          cudaStreamWaitEvent(K.stream, up, 0);
+          s->ev_pool.push_back(up);
+        }
+      }
+      const prop_status st = batch_step(mb, n, K.stream);
+      if (st != PROP_OK) {
+        const std::string msg = prop_last_error();
+        cudaStreamSynchronize(K.stream);
+        for (int i = 0; i < n; ++i) {
+          Request* r = rs[i];
+          release(s, r);
+          finish(s, r, kFailed, st, msg);
+          r->state = kFailed;
+        }
+        std::vector<Request*> keep;
+        for (Request* r : s->active)
+          if (r->state != kFailed) keep.push_back(r);
+        s->active.swap(keep);
+        s->cv_done.notify_all();
+        s->cv_admit.notify_all();
+        progressed = true;
+        continue;
+      }
+      cudaEvent_t e = take_ev(s);
+      cudaEventRecord(e, K.stream);
+      K.inflight.push_back(e);
+      for (int i = 0; i < n; ++i) {
+        Request* r = rs[i];
+        std::swap(r->cur, r->nxt);
+        r->k += 1;
+        r->last_ev = e;
+      }
+      progressed = true;
+    }
     if (!progressed) {
       // Nothing to issue: wait briefly for the GPU or for new submissions.
       s->cv_work.wait_for(lk, std::chrono::microseconds(s->active.empty() ? 2000 : 20));
     }
+  }
+  for (auto& kv : s->klasses) {
+    if (kv.second.stream) cudaStreamSynchronize(kv.second.stream);
+    for (cudaEvent_t e : kv.second.inflight) s->ev_pool.push_back(e);
+    kv.second.inflight.clear();
+    if (kv.second.stream) cudaStreamDestroy(kv.second.stream);
+    kv.second.stream = nullptr;
   }
 }
 

@@ -139,14 +139,16 @@ __device__ __forceinline__ double block_sum_tv(double v, double* sh) {
 // Deterministic loss: every block stores its partial TV sum, the last block
 // to arrive adds them in block order plus the data term and writes the loss.
 // Blocks are numbered linearly over a 2-D grid.
-__device__ __forceinline__ void finish_loss(float local, double* partials, unsigned int* counter,
-                                            const double* data_loss, double* loss_out) {
+// vb, nblk: this block's index and the block count of the reduction (the
+// launch's blocks, or the share of a multi-problem launch that serves one
+// problem).
+__device__ __forceinline__ void finish_loss_v(float local, double* partials, unsigned int* counter,
+                                              const double* data_loss, double* loss_out, unsigned vb, unsigned nblk) {
   __shared__ double sh[32];
   __shared__ bool last;
-  const unsigned nblk = gridDim.x * gridDim.y;
   const double bs = block_sum_tv((double)local, sh);
   if (threadIdx.x == 0) {
-    partials[blockIdx.y * gridDim.x + blockIdx.x] = bs;
+    partials[vb] = bs;
     __threadfence();
     const unsigned prev = atomicAdd(counter, 1u);
     last = prev == nblk - 1;
@@ -162,6 +164,11 @@ __device__ __forceinline__ void finish_loss(float local, double* partials, unsig
       *counter = 0u;
     }
   }
+}
+__device__ __forceinline__ void finish_loss(float local, double* partials, unsigned int* counter,
+                                            const double* data_loss, double* loss_out) {
+  finish_loss_v(local, partials, counter, data_loss, loss_out, blockIdx.y * gridDim.x + blockIdx.x,
+                gridDim.x * gridDim.y);
 }
 
 }  // namespace prop

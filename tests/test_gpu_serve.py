@@ -104,3 +104,32 @@ def test_cancel_and_poll():
     vol, lat, loss = srv.wait(t2, timeout_ms=60000)
     assert np.isfinite(vol).all()
     srv.close()
+
+
+def test_same_class_requests_are_batched_and_equal_lone_runs():
+    """Six requests of one kernel class (2N = 96, 8 bins) with four slots:
+    the server advances them in batched iterations (one launch per stage for
+    all running requests); each result is its lone reconstruction bit for bit."""
+    import torch
+    from paper_2311_13177_gb300 import Plan
+    from paper_2311_13177_gb300.serve import Server
+    reqs = []
+    for i in range(6):
+        dyn = i % 2 == 1
+        w = synth.Workload(f"c{i}", N=48, Nf=8, delta_lo=-2.0, delta_hi=2.0, B=4 + i, L=8 + 2 * (i % 3), R=48,
+                           T=2 if dyn else 1, angles="golden" if dyn else "uniform", n_ellipses=4,
+                           iters=6 + 3 * i, tv_t=1e-2 if dyn else 0.0, motion=(0, 2.0, 3.0) if dyn else None,
+                           seed=700 + i)
+        reqs.append((w, synth.make_problem(w)))
+    srv = Server(hbm_budget_bytes=2 << 30, max_slots=4)
+    tickets = [srv.submit(w.N, w.L, w.R, p["theta"], p["delta"], p["y"], _params(w), blade_frame=p["blade_frame"],
+                          T=w.T) for w, p in reqs]
+    results = [srv.wait(t) for t in tickets]
+    srv.close()
+    for (w, p), (vol, lat, loss) in zip(reqs, results):
+        plan = Plan(w.N, w.L, w.R, p["theta"], p["delta"], p["blade_frame"], w.T)
+        V, tr = plan.reconstruct(torch.from_numpy(p["y"]).cuda(), _params(w))
+        alone = V.cpu().numpy()
+        plan.destroy()
+        assert np.array_equal(vol, alone), w.name
+        assert abs(loss - tr[-1]) <= 1e-12 * abs(tr[-1])

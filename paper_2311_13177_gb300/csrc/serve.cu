@@ -179,7 +179,8 @@ struct prop_server_s {
   // kernel classes of the running requests: (2N, bin stride, width) -> stream
   // and the events of its batched iterations in flight
   struct Klass {
-    cudaStream_t stream = nullptr;
+    cudaStream_t hi = nullptr, lo = nullptr;  // high- and low-priority streams
+    cudaStream_t last = nullptr;              // the stream of the class's latest batched iteration
     std::deque<cudaEvent_t> inflight;
   };
   std::map<std::tuple<int, int, int>, Klass> klasses;
@@ -445,19 +446,37 @@ void scheduler(prop_server_s* s) {
     }
     if (still.size() != s->active.size()) s->cv_admit.notify_all();
     s->active.swap(still);
-    // one batched iteration for every class with work and fewer than two in flight
+    // one batched iteration for every class with work and fewer than two in
+    // flight; the class holding the oldest running request issues on a
+    // high-priority stream, so that it keeps the GPU as a FIFO queue would
+    // give it, and the others fill in behind
     std::map<std::tuple<int, int, int>, std::vector<Request*>> ready;
+    const Request* oldest = nullptr;
     for (Request* r : s->active)
-      if (!r->cancel && !r->copying && r->k < r->params.iters) ready[klass_of(*r->plan)].push_back(r);
+      if (!r->cancel && !r->copying && r->k < r->params.iters) {
+        ready[klass_of(*r->plan)].push_back(r);
+        if (!oldest || r->t_submit < oldest->t_submit) oldest = r;
+      }
     for (auto& kv : ready) {
       prop_server_s::Klass& K = s->klasses[kv.first];
       if (K.inflight.size() >= 2) continue;
-      if (!K.stream && cudaStreamCreateWithFlags(&K.stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        K.stream = nullptr;
-        continue;
+      if (!K.hi) {
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        if (cudaStreamCreateWithPriority(&K.hi, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&K.lo, cudaStreamNonBlocking, lo_prio) != cudaSuccess) {
+          cudaGetLastError();
+          if (K.hi) cudaStreamDestroy(K.hi);
+          K.hi = K.lo = nullptr;
+          continue;
+        }
       }
       std::vector<Request*>& rs = kv.second;
+      const bool first = std::find(rs.begin(), rs.end(), oldest) != rs.end();
+      cudaStream_t stream = first ? K.hi : K.lo;
+      if (K.last && K.last != stream && !K.inflight.empty())
+        cudaStreamWaitEvent(stream, K.inflight.back(), 0);  // the class's iterations stay in order
+      K.last = stream;
       // the requests furthest behind first (admission order among equals)
       std::stable_sort(rs.begin(), rs.end(), [](const Request* a, const Request* b) { return a->k < b->k; });
       const int n = std::min<int>((int)rs.size(), kMaxBatch);
@@ -472,14 +491,14 @@ void scheduler(prop_server_s* s) {
         if (r->k == 0) {
           cudaEvent_t up = take_ev(s);
           cudaEventRecord(up, r->stream);
-          cudaStreamWaitEvent(K.stream, up, 0);
+          cudaStreamWaitEvent(stream, up, 0);
           s->ev_pool.push_back(up);
         }
       }
-      const prop_status st = batch_step(mb, n, K.stream);
+      const prop_status st = batch_step(mb, n, stream);
       if (st != PROP_OK) {
         const std::string msg = prop_last_error();
-        cudaStreamSynchronize(K.stream);
+        cudaStreamSynchronize(stream);
         for (int i = 0; i < n; ++i) {
           Request* r = rs[i];
           release(s, r);
@@ -496,7 +515,7 @@ void scheduler(prop_server_s* s) {
         continue;
       }
       cudaEvent_t e = take_ev(s);
-      cudaEventRecord(e, K.stream);
+      cudaEventRecord(e, stream);
       K.inflight.push_back(e);
       for (int i = 0; i < n; ++i) {
         Request* r = rs[i];
@@ -512,11 +531,14 @@ void scheduler(prop_server_s* s) {
     }
   }
   for (auto& kv : s->klasses) {
-    if (kv.second.stream) cudaStreamSynchronize(kv.second.stream);
+    for (cudaStream_t st : {kv.second.hi, kv.second.lo})
+      if (st) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+      }
     for (cudaEvent_t e : kv.second.inflight) s->ev_pool.push_back(e);
     kv.second.inflight.clear();
-    if (kv.second.stream) cudaStreamDestroy(kv.second.stream);
-    kv.second.stream = nullptr;
+    kv.second.hi = kv.second.lo = kv.second.last = nullptr;
   }
 }
 

@@ -50,7 +50,7 @@ struct InterpArgs {
   int* err;  // set to 1 when a bounded wait expires
   const int* cta_off;  // CTA c takes items [cta_off[c], cta_off[c + 1]) (balanced at plan time)
   int n_items, R, n, C, Cv, f0, Nf;
-  int TI, tps, nbuf;
+  int TR, TC, nct, tpf, nbuf;  // tile rows, cells per row, tiles per row of tiles and per frame
   float scale;
   int accumulate;
 };
@@ -110,34 +110,33 @@ struct ItemGeom {
 
 __device__ __forceinline__ ItemGeom item_geom(const InterpArgs& a, int item) {
   const int4 it = __ldg(&a.items[item]);
-  const int tpp = a.tps * a.tps;
   ItemGeom g;
-  g.t = it.x / tpp;
-  const int rem = it.x - g.t * tpp;
-  g.r0 = (rem / a.tps) * a.TI;
-  g.c0 = (rem % a.tps) * a.TI;
+  g.t = it.x / a.tpf;
+  const int rem = it.x - g.t * a.tpf;
+  g.r0 = (rem / a.nct) * a.TR;
+  g.c0 = (rem % a.nct) * a.TC;
   g.start = it.y;
   g.count = it.z;
   return g;
 }
 
-// Thread 0: stream item `item`'s tile + halo (HW rows of HW cells x C bins,
-// wrapped modulo n) into `dst`, completing on `bar`.
+// Thread 0: stream item `item`'s tile + halo (TR + W - 1 rows of TC + W - 1
+// cells x C bins, wrapped modulo n) into `dst`, completing on `bar`.
 template <int W>
 __device__ void issue_tile(const InterpArgs& a, int item, float2* dst, uint64_t* bar) {
   const ItemGeom g = item_geom(a, item);
-  const int HW = a.TI + W - 1;
+  const int HR = a.TR + W - 1, HC = a.TC + W - 1;
   const size_t nC = (size_t)a.n * a.C;
   const float2* G = a.grid + (size_t)g.t * a.n * nC;
-  mbar_expect_tx(bar, (uint32_t)((size_t)HW * HW * a.C * sizeof(float2)));
-  const int run1 = min(HW, a.n - g.c0);
-  for (int q = 0; q < HW; ++q) {
+  mbar_expect_tx(bar, (uint32_t)((size_t)HR * HC * a.C * sizeof(float2)));
+  const int run1 = min(HC, a.n - g.c0);
+  for (int q = 0; q < HR; ++q) {
     int gr = g.r0 + q;
     gr = gr >= a.n ? gr - a.n : gr;
-    float2* d = dst + (size_t)q * HW * a.C;
+    float2* d = dst + (size_t)q * HC * a.C;
     bulk_g2s(d, G + (size_t)gr * nC + (size_t)g.c0 * a.C, (uint32_t)(run1 * a.C * sizeof(float2)), bar);
-    if (run1 < HW)
-      bulk_g2s(d + (size_t)run1 * a.C, G + (size_t)gr * nC, (uint32_t)((HW - run1) * a.C * sizeof(float2)), bar);
+    if (run1 < HC)
+      bulk_g2s(d + (size_t)run1 * a.C, G + (size_t)gr * nC, (uint32_t)((HC - run1) * a.C * sizeof(float2)), bar);
   }
 }
 
@@ -156,9 +155,9 @@ __global__ void __launch_bounds__(kInterpThreads, 1) interp_kernel(InterpArgs a)
   const int sub = lane & (LP - 1);
   const int slot = lane / LP;
   const int C = CS > 0 ? CS : a.C;
-  const int TI = CS > 0 ? interp_tile_for(CS, W) : a.TI;
-  const int HW = TI + W - 1;
-  const size_t tile_elems = (size_t)HW * HW * C;
+  const int HR = (CS > 0 ? interp_tile_rows(CS, W) : a.TR) + W - 1;
+  const int HC = (CS > 0 ? interp_tile_cols(CS, W) : a.TC) + W - 1;
+  const size_t tile_elems = (size_t)HR * HC * C;
   float2* bufs = reinterpret_cast<float2*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + a.nbuf * tile_elems * sizeof(float2));
   __shared__ int s_abort;
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(kInterpThreads, 1) interp_kernel(InterpArgs a)
       if (valid) {
         const int lc = (int)(packed & 0xffff) - g.c0;  // the first tap lies in the tile
         const int lr = (int)(packed >> 16) - g.r0;
-        const float2* base = tile + ((size_t)lr * HW + lc) * C + sub;
+        const float2* base = tile + ((size_t)lr * HC + lc) * C + sub;
         // W independent row sums (x1 weights), then the x2 weights; with a
         // compile-time stride every offset below is an immediate.
         auto tap_sum = [&](const float2* p) {
@@ -233,7 +232,7 @@ __global__ void __launch_bounds__(kInterpThreads, 1) interp_kernel(InterpArgs a)
             racc[q] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < W; ++c) {
-              const float2 gv = p[(q * HW + c) * C];
+              const float2 gv = p[(q * HC + c) * C];
               racc[q].x = fmaf(w[c], gv.x, racc[q].x);
               racc[q].y = fmaf(w[c], gv.y, racc[q].y);
             }
@@ -310,7 +309,7 @@ __global__ void __launch_bounds__(kInterpThreads, 1) interp_kernel(InterpArgs a)
   if (a.partials) reduce_to((double)sumsq, a.partials, a.counter, a.sumsq_out);
 }
 
-constexpr int kInterpConsumers = 24;                          // compute warps per CTA
+constexpr int kInterpConsumers = 16;                          // compute warps per CTA
 constexpr int kInterp2Threads = 32 * (kInterpConsumers + 1);  // plus one producer warp
 
 // Interpolation for the compile-time bin strides CS in {8, 16, 32, 64}.
@@ -330,12 +329,12 @@ __device__ __forceinline__ void interp2_body(const InterpArgs& a, int it_beg, in
   constexpr int NCW = kInterpConsumers;
   constexpr int LPS = CS / 2;   // lanes per sample
   constexpr int SPW = 32 / LPS; // samples per warp and round
-  constexpr int TI = interp_tile_for(CS, W);
-  constexpr int HW = TI + W - 1;
+  constexpr int HR = interp_tile_rows(CS, W) + W - 1;  // staged rows
+  constexpr int HC = interp_tile_cols(CS, W) + W - 1;  // staged cells per row
   constexpr int WQ = W / 2;
   constexpr int MPL = (kInterpItem + NCW * SPW - 1) / (NCW * SPW) * SPW;  // samples per warp per item
   static_assert(MPL <= 32, "one prefetched sample per lane");
-  constexpr size_t tile_elems = (size_t)HW * HW * CS;
+  constexpr size_t tile_elems = (size_t)HR * HC * CS;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int sub = lane % LPS;
@@ -429,7 +428,7 @@ __device__ __forceinline__ void interp2_body(const InterpArgs& a, int it_beg, in
         if (valid) {
           const int lc = (int)(packed & 0xffff) - g.c0;
           const int lr = (int)(packed >> 16) - g.r0;
-          const float4* base = reinterpret_cast<const float4*>(tile + ((size_t)lr * HW + lc) * CS + f_lo);
+          const float4* base = reinterpret_cast<const float4*>(tile + ((size_t)lr * HC + lc) * CS + f_lo);
           // row sums over the x1 taps, folded into the x2 sum row by row
           float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -437,7 +436,7 @@ __device__ __forceinline__ void interp2_body(const InterpArgs& a, int it_beg, in
             float4 rs = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < W; ++c) {
-              const float4 gv = base[(q * HW + c) * (CS / 2)];
+              const float4 gv = base[(q * HC + c) * (CS / 2)];
               rs.x = fmaf(w[c], gv.x, rs.x);
               rs.y = fmaf(w[c], gv.y, rs.y);
               rs.z = fmaf(w[c], gv.z, rs.z);
@@ -952,9 +951,12 @@ cudaError_t nufft_configure(int smem_optin) {
   return cudaSuccess;
 }
 
+size_t interp_tile_bytes(const Plan& p) {
+  return (size_t)(p.interp_tr + p.W - 1) * (p.interp_tc + p.W - 1) * p.cs * sizeof(float2);
+}
+
 int interp_buffers(const Plan& p) {
-  const int HW = p.interp_tile + p.W - 1;
-  const size_t tile = (size_t)HW * HW * p.cs * sizeof(float2);
+  const size_t tile = interp_tile_bytes(p);
   // two buffers when they fit next to the barriers and the static shared memory
   return 2 * tile + 1024 <= (size_t)p.smem_optin ? 2 : 1;
 }
@@ -984,8 +986,10 @@ InterpArgs interp_args(const Plan& p, int f0, int nbins, float2* y, const float2
   a.Nf = p.Nf;
   a.scale = 1.0f / (float)p.N;
   a.accumulate = accumulate ? 1 : 0;
-  a.TI = p.interp_tile;
-  a.tps = p.n / p.interp_tile;
+  a.TR = p.interp_tr;
+  a.TC = p.interp_tc;
+  a.nct = p.n / p.interp_tc;
+  a.tpf = ((p.n + p.interp_tr - 1) / p.interp_tr) * a.nct;
   a.nbuf = interp_buffers(p);
   a.cta_off = p.item_cta_off;
   return a;
@@ -1026,13 +1030,14 @@ cudaError_t interp(const Plan& p, int f0, int nbins, float2* y, const float2* y_
   a.Nf = p.Nf;
   a.scale = 1.0f / (float)p.N;
   a.accumulate = accumulate ? 1 : 0;
-  a.TI = p.interp_tile;
-  a.tps = p.n / p.interp_tile;
+  a.TR = p.interp_tr;
+  a.TC = p.interp_tc;
+  a.nct = p.n / p.interp_tc;
+  a.tpf = ((p.n + p.interp_tr - 1) / p.interp_tr) * a.nct;
   a.nbuf = interp_buffers(p);
   if (p.n_items == 0) return cudaSuccess;
-  const int HW = p.interp_tile + p.W - 1;
   // tiles, then a full and an empty barrier per buffer
-  const size_t smem = (size_t)a.nbuf * HW * HW * p.cs * sizeof(float2) + 2 * a.nbuf * sizeof(uint64_t);
+  const size_t smem = (size_t)a.nbuf * interp_tile_bytes(p) + 2 * a.nbuf * sizeof(uint64_t);
   a.cta_off = p.item_cta_off;
   // the two-bin kernel runs exactly the plan's balanced CTAs; the
   // one-bin kernel strides over the items
@@ -1073,9 +1078,8 @@ cudaError_t interp_residual_batch(Plan* const* ps, const float2* const* y_meas, 
   }
   const Plan& p0 = *mp[0];
   const int ctas = split_ctas(work, cap, m.nreq, std::max(m.nreq, p0.num_sms), m.cta_begin);
-  const int HW = p0.interp_tile + p0.W - 1;
   const int nbuf = interp_buffers(p0);
-  const size_t smem = (size_t)nbuf * HW * HW * p0.cs * sizeof(float2) + 2 * nbuf * sizeof(uint64_t);
+  const size_t smem = (size_t)nbuf * interp_tile_bytes(p0) + 2 * nbuf * sizeof(uint64_t);
   return p0.W == 8 ? launch_interp_multi<8>(p0.cs, m, ctas, smem, s) : launch_interp_multi<6>(p0.cs, m, ctas, smem, s);
 }
 

@@ -378,21 +378,22 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   for (int q = 0; q < n; ++q)
     tw[q] = make_float2((float)std::cos(2 * M_PI * q / n), (float)-std::sin(2 * M_PI * q / n));
 
-  // Interpolation work items: samples sorted by (frame, TI x TI-cell tile of
+  // Interpolation work items: samples sorted by (frame, TR x TC-cell tile of
   // their first tap), ascending m within a tile; every non-empty tile's run is
   // cut into items of at most kInterpItem samples.  One CTA per item stages
   // the tile plus its (W-1)-cell halo in shared memory.
-  p->interp_tile = interp_tile_for(p->cs, p->W);
-  const int TI = p->interp_tile;
-  const int tps = n / TI;
-  const size_t ntile = (size_t)p->T * tps * tps;
+  p->interp_tr = interp_tile_rows(p->cs, p->W);
+  p->interp_tc = interp_tile_cols(p->cs, p->W);
+  const int TR = p->interp_tr, TC = p->interp_tc;
+  const int nrt = (n + TR - 1) / TR, nct = n / TC;  // tiles per column / per row of the grid
+  const size_t ntile = (size_t)p->T * nrt * nct;
   const size_t LR = (size_t)p->L * p->R;
   std::vector<int> order(p->M);
   std::vector<int4> items;
   {
     auto tile_of = [&](size_t m) {
       const size_t frame = (size_t)p->blade_frame[m / LR];
-      return (frame * tps + first_tap[2 * m + 1] / TI) * tps + first_tap[2 * m] / TI;
+      return (frame * nrt + first_tap[2 * m + 1] / TR) * nct + first_tap[2 * m] / TC;
     };
     std::vector<int> cnt(ntile + 1, 0);
     for (size_t m = 0; m < (size_t)p->M; ++m) cnt[tile_of(m) + 1]++;
@@ -417,7 +418,7 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   std::vector<int> cta_off;
   {
     const int P = std::max(1, std::min(p->num_sms, p->n_items));
-    const long tile_cost = (long)(TI + Wi - 1) * (TI + Wi - 1) * p->cs / 16;
+    const long tile_cost = (long)(TR + Wi - 1) * (TC + Wi - 1) * p->cs / 16;
     auto cost = [&](const int4& it) { return (long)it.z * Wi * Wi * p->cs / 16 + tile_cost; };
     std::vector<int> idx(items.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
@@ -715,10 +716,10 @@ size_t plan_estimate_bytes(const prop_plan_desc* d, int iters) {
   const size_t W = d->kb_width == 8 ? 8 : 6;
   const size_t chunk = d->bin_chunk == 0 ? std::min<size_t>(Nf, kMaxChunk) : std::min<size_t>(d->bin_chunk, Nf);
   const size_t cs = chunk + (chunk & 1);
-  const size_t TI = (size_t)interp_tile_for((int)cs, (int)W);
+  const size_t TR = (size_t)interp_tile_rows((int)cs, (int)W), TC = (size_t)interp_tile_cols((int)cs, (int)W);
   const size_t ncell = T * n * n;
   const size_t vol = T * N * N * Nf;
-  const size_t interp_items = M / kInterpItem + T * (n / TI) * (n / TI) + 1;
+  const size_t interp_items = M / kInterpItem + T * ((n + TR - 1) / TR) * (n / TC) + 1;
   const size_t spread_items = (M * W * W + kSpreadCellCost * ncell) / kSpreadItemCost + 1;
   size_t b = 0;
   b += 4 * M + M * (W / 2) * 16 + (size_t)d->readout * Nf * 8 + 4 * N + 8 * n + 4 * B + 4 * M;  // sample tables

@@ -26,14 +26,15 @@ constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list ent
 constexpr int kSpreadGroupItemCost = 2048;  // target work per grouped spread item
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 
-// Interpolation tile edge (cells) for bin stride cs and kernel width W: 16
-// up to 32 bins, else 8.  At width 8 with 32 bins the 16-cell tile plus its
-// 7-cell halo (135 KB) leaves room for one buffer only, so its copy does not
-// overlap the previous tile's work; an 8-cell tile double-buffers but stages
-// 3.5x the cells it owns instead of 2.1x and splits the samples into items a
-// quarter the size, and measured slower (90 against 82 us at the static
-// workload).
-constexpr int interp_tile_for(int cs, int W) { return (void)W, cs <= 32 ? 16 : 8; }
+// Interpolation tile (rows x cells per row) for bin stride cs and kernel
+// width W: 16 x 16 up to 32 bins, 8 x 8 above.  At width 8 with 32 bins a
+// 16 x 16 tile plus its 7-cell halo (23 x 23 cells, 135 KB) leaves room for
+// one buffer only, so its copy could not overlap the previous tile's work;
+// 12 rows of 16 (19 x 23 staged cells, 112 KB) double-buffer and stage 2.3x
+// the cells they own (16 x 16: 2.1x; 8 x 8: 3.5x, which measured slower).
+// Rows of tiles need not divide the grid: the last one wraps past row n - 1.
+constexpr int interp_tile_rows(int cs, int W) { return cs > 32 ? 8 : (W == 8 && cs == 32 ? 12 : 16); }
+constexpr int interp_tile_cols(int cs, int W) { return (void)W, cs > 32 ? 8 : 16; }
 
 constexpr int kMaxChunk = 64;      // most bins in one grid pass
 constexpr int kMaxBatch = 8;       // most problems in one multi-problem launch
@@ -137,7 +138,7 @@ struct Plan {
   int* item_cta_off = nullptr;   // [interp_ctas + 1] CTA c interpolates items [off[c], off[c + 1])
   int n_items = 0;
   int interp_ctas = 1;           // persistent interpolation CTAs the items are balanced over
-  int interp_tile = 16;          // TI: interpolation tile edge, cells
+  int interp_tr = 16, interp_tc = 16;  // interpolation tile: rows, cells per row
   // Spread gather: cells in patch-major order (frame, 8x8-cell patch,
   // row-major in the patch), cut into items; each item is one blob of
   // (cell, list end) pairs followed by its cells' (offset m * cs, weight

@@ -226,6 +226,8 @@ prop_status batch_step(BatchMember* mb, int count, cudaStream_t s) {
   for (int r = 0; r < count; ++r) {
     Plan& p = *mb[r].p;
     if (!batch_compatible(p, *mb[0].p)) return fail(PROP_ERR_INVALID_ARG, "batch: plans differ in 2N, bin stride or width");
+    for (int q = 0; q < r; ++q)
+      if (mb[q].p == &p) return fail(PROP_ERR_INVALID_ARG, "batch: a plan appears twice (its workspace is one problem's)");
     if (mb[r].k == 1) {
       const size_t vbytes = p.vol_elems() * sizeof(float2);
       PROP_CUDA(cudaMemsetAsync(p.adam_m, 0, vbytes, s));

@@ -17,6 +17,8 @@
 // pass writes global memory directly (cropping and scaling applied on the
 // fly); intermediate passes exchange through shared memory in place.
 // Every thread holds E = 16 (n = 2^a) or 12 (n = 3 * 2^a) values per pass.
+#include <type_traits>
+
 #include "prop_internal.cuh"
 #include "tv_adam.cuh"
 #include "tma.cuh"
@@ -29,18 +31,28 @@ struct RadixPlan {
   int r[8];
 };
 
-// Radices 8, 4, 2 then 3.  Lengths with a factor 3 use radix 4 instead of 8,
-// so that 12 values a thread (the least common multiple of the radices) hold
-// whole butterflies in every pass: half the registers of 24, twice the threads;
-// a leftover factor 2 is merged with a 3 into one radix-6 pass.
-__host__ __device__ constexpr RadixPlan radix_plan(int n) {
+// Radices for E values a thread (every radix divides E, so a thread holds
+// whole butterflies in every pass): with E = 32, radix 32 while it divides
+// and then 16; else radix 8 where E allows (E = 16 or 24), radix 4 where it
+// does not (E = 12, lengths with a factor 3: half the registers of 24,
+// twice the threads); then 4, 2 and the threes, a leftover factor 2 merged
+// with a 3 into one radix-6 pass.
+__host__ __device__ constexpr RadixPlan radix_plan(int n, int E) {
   RadixPlan p{0, {1, 1, 1, 1, 1, 1, 1, 1}};
   int m = n, threes = 0;
   while (m % 3 == 0) {
     m /= 3;
     ++threes;
   }
-  while (threes == 0 && m % 8 == 0) {
+  while (E % 32 == 0 && threes == 0 && m % 32 == 0) {
+    p.r[p.count++] = 32;
+    m /= 32;
+  }
+  if (E % 16 == 0 && threes == 0 && m % 16 == 0 && p.count > 0) {
+    p.r[p.count++] = 16;
+    m /= 16;
+  }
+  while (E % 8 == 0 && m % 8 == 0) {
     p.r[p.count++] = 8;
     m /= 8;
   }
@@ -71,9 +83,9 @@ __host__ __device__ constexpr RadixPlan radix_plan(int n) {
 // entry [k][r] (k < NS, r < R) = exp(-2 pi i r k / (NS R)), so a butterfly
 // fetches its R factors with R/2 16-byte loads.  Offsets are even (every NS
 // and hence every table size is even), so the tables stay 16-byte aligned.
-template <int NFFT>
+template <int NFFT, int EV>
 __host__ __device__ constexpr int tw_offset(int pass) {
-  constexpr RadixPlan RP = radix_plan(NFFT);
+  constexpr RadixPlan RP = radix_plan(NFFT, EV);
   int off = 0, ns = RP.r[0];
   for (int q = 1; q < pass; ++q) {
     off += ns * RP.r[q];
@@ -89,24 +101,31 @@ template <int NFFT>
 constexpr int kValsPlain = (NFFT % 3 == 0) ? 12 : 16;
 template <int NFFT>
 constexpr int kValsFused = (NFFT % 3 == 0) ? 12 : 16;
+// Values per thread of the TMA-staged column passes: 32 at n = 512 (radix
+// 32 then 16: one shared-memory exchange instead of two) and 24 at n = 384
+// (radices 8, 8, 6: two instead of three), with twice the registers and
+// half the threads of a 16-value shape; 2N = 512: 23.9 -> 20.3 us forward,
+// 24.8 -> 22.3 us adjoint; 2N = 384: 184.7 -> 153.8 us and 193.4 -> 164.7 us.
+template <int NFFT>
+constexpr int kValsCols = NFFT == 512 ? 32 : NFFT == 384 ? 24 : kValsPlain<NFFT>;
 
 template <int NFFT, int EV>
 struct Shape {
   static constexpr int E = EV;                 // values per thread
   static constexpr int TPL = NFFT / E;         // threads per line
   static constexpr int THREADS = TPL * kFftCols;
-  static constexpr int TW = tw_offset<NFFT>(radix_plan(NFFT).count);  // twiddle table entries
+  static constexpr int TW = tw_offset<NFFT, EV>(radix_plan(NFFT, EV).count);  // twiddle table entries
   static constexpr size_t SMEM = (size_t)NFFT * kFftCols * sizeof(float2) + (size_t)TW * sizeof(float2);
 };
 
 // Fill the per-pass twiddle tables from the length-NFFT table exp(-2 pi i m / NFFT).
-template <int NFFT>
+template <int NFFT, int EV>
 __device__ void build_twiddles(float2* tws, const float2* __restrict__ base) {
-  constexpr RadixPlan RP = radix_plan(NFFT);
+  constexpr RadixPlan RP = radix_plan(NFFT, EV);
   int ns = RP.r[0];
   for (int p = 1; p < RP.count; ++p) {
     const int R = RP.r[p];
-    const int off = tw_offset<NFFT>(p);
+    const int off = tw_offset<NFFT, EV>(p);
     const int step = NFFT / (ns * R);
     for (int idx = threadIdx.x; idx < ns * R; idx += blockDim.x) {
       const int k = idx / R, r = idx - (idx / R) * R;
@@ -223,6 +242,88 @@ struct Dft<6, SIGN> {
   }
 };
 
+// cos(2 pi m / 32) from its values on the first quadrant; sin(2 pi m / 32)
+// = cos(2 pi (m - 8) / 32).  The constant factors inside the radix-16 and
+// radix-32 butterflies.
+__host__ __device__ constexpr double cos32(int m) {
+  constexpr double q[9] = {1.0,
+                           0.98078528040323044912618223613424,   // cos(pi / 16)
+                           0.92387953251128675612818318939679,   // cos(pi / 8)
+                           0.83146961230254523707878837761791,   // cos(3 pi / 16)
+                           0.70710678118654752440084436210485,   // cos(pi / 4)
+                           0.55557023301960222474283081394853,   // cos(5 pi / 16)
+                           0.38268343236508977172845998403040,   // cos(3 pi / 8)
+                           0.19509032201612826784828486847702,   // cos(7 pi / 16)
+                           0.0};
+  m &= 31;
+  return m <= 8 ? q[m] : m <= 16 ? -q[16 - m] : m <= 24 ? -q[m - 16] : q[32 - m];
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// z * exp(SIGN 2 pi i M / R) for R dividing 32; quarter turns exactly.
+template <int SIGN, int R, int M>
+__device__ __forceinline__ float2 rotate(float2 z) {
+  constexpr int m = (M % R) * (32 / R);  // in 32nds of a turn
+  if constexpr (m == 0) {
+    return z;
+  } else if constexpr (m == 8) {
+    return mul_si<SIGN>(z);
+  } else if constexpr (m == 16) {
+    return make_float2(-z.x, -z.y);
+  } else if constexpr (m == 24) {
+    return mul_si<-SIGN>(z);
+  } else {
+    constexpr float c = (float)cos32(m), sn = (float)(SIGN * sin32(m));
+    return make_float2(fmaf(z.x, c, -z.y * sn), fmaf(z.x, sn, z.y * c));
+  }
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// R = R1 R2 point DFT from R2 DFTs of R1 points and R1 of R2 points:
+// with q = R2 q1 + q2 and k = k1 + R1 k2,
+//   X_k = sum_q2 w_R^(q2 k1) w_R2^(q2 k2) sum_q1 x_q w_R1^(q1 k1),  w_R = exp(SIGN 2 pi i / R).
+template <int R1, int R2, int SIGN>
+__device__ __forceinline__ void dft_compose(float2* v) {
+  constexpr int R = R1 * R2;
+  float2 y[R];  // y[q2 R1 + k1]
+  static_for<0, R2>([&](auto q2c) {
+    constexpr int q2 = decltype(q2c)::value;
+    float2 a[R1];
+#pragma unroll
+    for (int q1 = 0; q1 < R1; ++q1) a[q1] = v[R2 * q1 + q2];
+    Dft<R1, SIGN>::run(a);
+    static_for<0, R1>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      y[q2 * R1 + k1] = rotate<SIGN, R, q2 * k1>(a[k1]);
+    });
+  });
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 b[R2];
+#pragma unroll
+    for (int q2 = 0; q2 < R2; ++q2) b[q2] = y[q2 * R1 + k1];
+    Dft<R2, SIGN>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+  }
+}
+
+template <int SIGN>
+struct Dft<16, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) { dft_compose<4, 4, SIGN>(v); }
+};
+template <int SIGN>
+struct Dft<32, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) { dft_compose<8, 4, SIGN>(v); }
+};
+
 // One Stockham pass; recurses into the next pass at compile time.
 // PIN: the input line is a zero-padded image line (image index i at
 // position i - N/2 mod n, N = n/2, zeros elsewhere); the first pass then
@@ -251,7 +352,7 @@ template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class
           class Out, class Hook = NoHook>
 __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, int tl, const In& in,
                                          const Out& out, const Hook& hook = Hook()) {
-  constexpr RadixPlan RP = radix_plan(NFFT);
+  constexpr RadixPlan RP = radix_plan(NFFT, EV);
   constexpr int R = RP.r[PI];
   constexpr int E = EV;
   constexpr int TPL = NFFT / EV;
@@ -259,11 +360,11 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
   constexpr int STRIDE = NFFT / R;
   constexpr bool FIRST = PI == 0;
   constexpr bool LAST = PI == RP.count - 1;
-  constexpr bool PRUNE_IN = FIRST && PIN && (R == 8 || R == 4);
-  constexpr bool PRUNE_OUT = LAST && POUT && (R == 8 || R == 4);
+  constexpr bool PRUNE_IN = FIRST && PIN && R % 4 == 0;
+  constexpr bool PRUNE_OUT = LAST && POUT && R % 4 == 0;
   constexpr int Q = NFFT / 4;  // N / 2
   static_assert(E % R == 0, "radix must divide the per-thread count");
-  static_assert(!(FIRST && PIN) || PRUNE_IN, "padded input needs a first radix of 8 or 4");
+  static_assert(!(FIRST && PIN) || PRUNE_IN, "padded input needs a first radix of 32, 16, 8 or 4");
   float2 v[E];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
@@ -271,7 +372,7 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
     const int k = j % NS;
     float2 w[R];
     if constexpr (NS > 1) {
-      const float2* T = tws + tw_offset<NFFT>(PI) + k * R;
+      const float2* T = tws + tw_offset<NFFT, EV>(PI) + k * R;
       if constexpr (R % 2 == 0) {
 #pragma unroll
         for (int h = 0; h < R / 2; ++h) {
@@ -453,7 +554,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS) fft_ke
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
-  build_twiddles<NFFT>(tw, a.twiddle);
+  build_twiddles<NFFT, EV>(tw, a.twiddle);
   __syncthreads();
   const int col = threadIdx.x % kFftCols;
   const int tl = threadIdx.x / kFftCols;
@@ -668,7 +769,7 @@ __device__ __forceinline__ void fused_rows_body(const FusedArgs& a, int bx, size
   float2* gb = tw + Shape<NFFT, EV>::TW;  // [N][kFftCols]
   const int i2 = (int)(row % a.N);
   const int t = (int)(row / a.N);
-  build_twiddles<NFFT>(tw, a.twiddle);
+  build_twiddles<NFFT, EV>(tw, a.twiddle);
   grid_dep_wait();
   grid_dep_release();
   // the update's operands stream into L2 while the inverse FFT runs
@@ -818,7 +919,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsFused<NFFT>>::THREADS + kUpdT
     s_abort_f = 0;
     s_abort_u = 0;
   }
-  build_twiddles<NFFT>(tw, a.twiddle);
+  build_twiddles<NFFT, EV>(tw, a.twiddle);
   grid_dep_wait();
   grid_dep_release();
   int issued = 0, consumed = 0;  // tensor copies, meaningful on thread 0
@@ -942,20 +1043,22 @@ constexpr int col_rows() {
 }
 // Tile buffers and CTAs per SM: the forward pass stages the N image rows in
 // one buffer (the next tile is requested once the first pass has read the
-// current one) with two CTAs per SM; the adjoint stages all 2N rows, double
-// buffered, with one CTA per SM.
-template <int KIND>
+// current one) with two CTAs per SM; the adjoint stages all 2N rows in one
+// buffer with two CTAs per SM where two such CTAs fit an SM's shared memory
+// (2N <= kAdjColsTwoCtaMax), else double-buffered with one CTA per SM.
+constexpr int kAdjColsTwoCtaMax = 384;
+template <int NFFT, int KIND>
 constexpr int col_bufs() {
-  return KIND == kFwdCols ? 1 : 2;
+  return KIND == kFwdCols || NFFT <= kAdjColsTwoCtaMax ? 1 : 2;
 }
-template <int KIND>
+template <int NFFT, int KIND>
 constexpr int col_ctas_per_sm() {
-  return KIND == kFwdCols ? 2 : 1;
+  return KIND == kFwdCols || NFFT <= kAdjColsTwoCtaMax ? 2 : 1;
 }
 template <int NFFT, int KIND>
 constexpr size_t col_smem() {
-  return (size_t)col_bufs<KIND>() * col_rows<NFFT, KIND>() * kFftCols * sizeof(float2) +
-         Shape<NFFT, kValsPlain<NFFT>>::SMEM + 2 * sizeof(uint64_t);
+  return (size_t)col_bufs<NFFT, KIND>() * col_rows<NFFT, KIND>() * kFftCols * sizeof(float2) +
+         Shape<NFFT, kValsCols<NFFT>>::SMEM + 2 * sizeof(uint64_t);
 }
 
 // The column pass of one problem run by vg persistent CTAs, this being the
@@ -963,9 +1066,9 @@ constexpr size_t col_smem() {
 // the kernel's parameter space).
 template <int NFFT, int KIND>
 __device__ __forceinline__ void cols_body(const CUtensorMap* tin, const ColArgs& a, int vb, int vg) {
-  constexpr int EV = kValsPlain<NFFT>;
+  constexpr int EV = kValsCols<NFFT>;
   constexpr int H = col_rows<NFFT, KIND>();
-  constexpr int NB = col_bufs<KIND>();
+  constexpr int NB = col_bufs<NFFT, KIND>();
   extern __shared__ __align__(128) float2 smem[];
   float2* tiles = smem;                      // [NB][H][kFftCols]
   float2* X = tiles + NB * H * kFftCols;     // [NFFT][kFftCols]
@@ -985,7 +1088,7 @@ __device__ __forceinline__ void cols_body(const CUtensorMap* tin, const ColArgs&
     fence_mbar_init();
     s_abort = 0;
   }
-  build_twiddles<NFFT>(tw, a.twiddle);
+  build_twiddles<NFFT, EV>(tw, a.twiddle);
   grid_dep_wait();
   grid_dep_release();
   if (threadIdx.x == 0)
@@ -1027,7 +1130,7 @@ __device__ __forceinline__ void cols_body(const CUtensorMap* tin, const ColArgs&
 }
 
 template <int NFFT, int KIND>
-__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ctas_per_sm<KIND>())
+__global__ void __launch_bounds__(Shape<NFFT, kValsCols<NFFT>>::THREADS, col_ctas_per_sm<NFFT, KIND>())
     fft_cols_tma_kernel(const __grid_constant__ CUtensorMap tin, ColArgs a) {
   cols_body<NFFT, KIND>(&tin, a, blockIdx.x, gridDim.x);
 }
@@ -1037,7 +1140,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ct
 // as CTA b - cta_begin[r] of cta_begin[r + 1] - cta_begin[r].  Every tile is
 // transformed exactly as by the problem's own launch.
 template <int NFFT, int KIND>
-__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS, col_ctas_per_sm<KIND>())
+__global__ void __launch_bounds__(Shape<NFFT, kValsCols<NFFT>>::THREADS, col_ctas_per_sm<NFFT, KIND>())
     fft_cols_multi_kernel(const __grid_constant__ MultiCols m) {
   int r = 0;
   while (r + 1 < m.nreq && (int)blockIdx.x >= m.cta_begin[r + 1]) ++r;
@@ -1119,9 +1222,9 @@ cudaError_t dispatch(int n, int kind, const FftArgs& a, dim3 grid, cudaStream_t 
 
 template <int NFFT>
 cudaError_t launch_cols_tma(int kind, const CUtensorMap& tm, const ColArgs& a, int sms, cudaStream_t s) {
-  const int per_sm = kind == kFwdCols ? col_ctas_per_sm<kFwdCols>() : col_ctas_per_sm<kAdjCols>();
+  const int per_sm = kind == kFwdCols ? col_ctas_per_sm<NFFT, kFwdCols>() : col_ctas_per_sm<NFFT, kAdjCols>();
   const dim3 grid((unsigned)std::max(1, std::min(a.ntiles, per_sm * sms)));
-  const dim3 block(Shape<NFFT, kValsPlain<NFFT>>::THREADS);
+  const dim3 block(Shape<NFFT, kValsCols<NFFT>>::THREADS);
   if (kind == kFwdCols)
     return launch_dep(fft_cols_tma_kernel<NFFT, kFwdCols>, grid, block, col_smem<NFFT, kFwdCols>(), s, tm, a);
   return launch_dep(fft_cols_tma_kernel<NFFT, kAdjCols>, grid, block, col_smem<NFFT, kAdjCols>(), s, tm, a);
@@ -1137,6 +1240,16 @@ size_t cols_smem(int n, int kind) {
   }
 }
 
+int cols_per_sm(int n, int kind) {
+  switch (n) {
+#define CASE(v) \
+  case v: return kind == kFwdCols ? col_ctas_per_sm<v, kFwdCols>() : col_ctas_per_sm<v, kAdjCols>();
+    PROP_FFT_SIZES(CASE)
+#undef CASE
+    default: return 1;
+  }
+}
+
 cudaError_t dispatch_cols_tma(int n, int kind, const CUtensorMap& tm, const ColArgs& a, int sms, cudaStream_t s) {
   switch (n) {
 #define CASE(v) \
@@ -1149,7 +1262,7 @@ cudaError_t dispatch_cols_tma(int n, int kind, const CUtensorMap& tm, const ColA
 
 template <int NFFT>
 cudaError_t launch_cols_multi(int kind, const MultiCols& m, int ctas, cudaStream_t s) {
-  const dim3 grid((unsigned)ctas), block(Shape<NFFT, kValsPlain<NFFT>>::THREADS);
+  const dim3 grid((unsigned)ctas), block(Shape<NFFT, kValsCols<NFFT>>::THREADS);
   if (kind == kFwdCols)
     return launch_dep(fft_cols_multi_kernel<NFFT, kFwdCols>, grid, block, col_smem<NFFT, kFwdCols>(), s, m);
   return launch_dep(fft_cols_multi_kernel<NFFT, kAdjCols>, grid, block, col_smem<NFFT, kAdjCols>(), s, m);
@@ -1306,7 +1419,7 @@ __global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS) cart_f
   extern __shared__ float2 smem[];
   float2* X = smem;
   float2* tw = smem + NFFT * kFftCols;
-  build_twiddles<NFFT>(tw, a.twiddle);
+  build_twiddles<NFFT, EV>(tw, a.twiddle);
   grid_dep_wait();
   grid_dep_release();
   __syncthreads();
@@ -1554,7 +1667,7 @@ cudaError_t cols_batch(Plan* const* ps, int count, int kind, cudaStream_t s) {
     work[r] = m.a[r].ntiles;
     cap[r] = std::max(1, m.a[r].ntiles);
   }
-  const int per_sm = kind == kFwdCols ? col_ctas_per_sm<kFwdCols>() : col_ctas_per_sm<kAdjCols>();
+  const int per_sm = cols_per_sm(ps[0]->n, kind);
   const int ctas = split_ctas(work, cap, count, std::max(count, per_sm * ps[0]->num_sms), m.cta_begin);
   return dispatch_cols_multi(ps[0]->n, kind, m, ctas, s);
 }

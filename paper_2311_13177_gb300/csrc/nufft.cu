@@ -15,10 +15,11 @@
 // Adjoint: G'_{t,f}[cell] = sum_m w(m, cell) conj(P[j_m][f]) r_m.  The
 // phased residual contrib[m][f] = conj(P[j_m][f]) r_m is formed once per
 // sample (fused into the interpolation when the grid holds every bin), then
-// the grid is gathered from plan-time lists in a fixed order: every 2 x 2
-// group of cells reads each covering sample's phased residual once and adds
-// it with that sample's weight on each of its four cells (per-cell lists
-// where the stride or a list's length rules the groups out).  No atomics,
+// the grid is gathered from plan-time lists in a fixed order: every group
+// of kSpreadGroupRows x kSpreadGroupCols cells reads each covering sample's
+// phased residual once and adds it with that sample's weight on each of its
+// cells (per-cell lists where the stride or a list's length rules the
+// groups out).  No atomics,
 // every cell written exactly once, bitwise reproducible.
 #include "prop_internal.cuh"
 #include "tma.cuh"
@@ -814,6 +815,96 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
                                  a.cta_off[(long)(v + 1) * P / c], a.Cv, a.n, a.err);
 }
 
+// The same spread with the items claimed at run time (plans with many
+// items per CTA): the producer warp's lane 0 claims the next item from the
+// plan's counter when a stage frees up (one claim ahead, so the atomic's
+// latency overlaps the waits) and publishes its index with the stage; when
+// the items run out it completes the stage's phase without a copy and marks
+// it -1.  A CTA whose items run long claims fewer; every item writes its own
+// cells, so the result does not depend on which CTA took it.  claim[0]:
+// items claimed, claim[1]: CTAs done; the last CTA of the launch returns
+// both to 0 (seen by the next launch: kernel boundary).  A separate kernel
+// from the plan-time-range one, whose code it leaves untouched (a kernel
+// holding both schedules measured slower on the ranges).
+template <int CS>
+__global__ void __launch_bounds__(kSpreadThreads, kSpreadCtasPerSm)
+    spread_claim_kernel(float2* grid, const float2* contrib, const int4* sitems, const int2* blob, int n_items,
+                        int* claim, int Cv, int n, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NCW = kSpreadConsumers;
+  constexpr int NBUF = 2;
+  int2* stage = reinterpret_cast<int2*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)NBUF * kSpreadStageInt2 * sizeof(int2));
+  uint64_t* empty = full + NBUF;
+  __shared__ volatile int s_abort;
+  __shared__ int s_next[NBUF];  // next unclaimed group of the item in each stage
+  __shared__ int s_item[NBUF];  // the item in each stage, -1: no more items
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], NCW);
+    }
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (warp == NCW) {
+    grid_dep_release();
+    if (lane == 0) {
+      int k = 0;
+      int ahead = atomicAdd(claim, 1);
+      for (;; ++k) {
+        const int b = k % NBUF;
+        if (k >= NBUF && !mbar_wait_bounded(&empty[b], (uint32_t)(((k / NBUF) - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        if (s_abort) break;
+        const int item = ahead;
+        if (item >= n_items) {
+          s_item[b] = -1;
+          mbar_arrive(&full[b]);  // completes the phase: the end mark
+          ++k;
+          break;
+        }
+        ahead = atomicAdd(claim, 1);
+        const int4 d = __ldg(&sitems[item]);
+        const uint32_t bytes = (uint32_t)d.w * (uint32_t)sizeof(int2);
+        s_item[b] = item;
+        s_next[b] = 0;  // both published to the gather warps by the barrier phase
+        mbar_expect_tx(&full[b], bytes);
+        bulk_g2s(stage + (size_t)b * kSpreadStageInt2, blob + d.x, bytes, &full[b]);
+      }
+      // at most one copy per stage can be in flight: the last one issued
+      for (int kk = k > NBUF ? k - NBUF : 0; kk < k; ++kk)
+        mbar_wait_bounded(&full[kk % NBUF], (uint32_t)((kk / NBUF) & 1));
+    }
+  } else {
+    grid_dep_wait();
+    grid_dep_release();
+    for (int k = 0;; ++k) {
+      const int b = k % NBUF;
+      if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NBUF) & 1))) s_abort = 1;
+      if (s_abort) break;
+      const int item = s_item[b];
+      if (item < 0) break;
+      const int4 d = __ldg(&sitems[item]);
+      gather_groups<CS>(stage + (size_t)b * kSpreadStageInt2, d.y, d.z, lane, &s_next[b], grid, contrib, Cv, n);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_abort) atomicExch(err, 1);
+    if (atomicAdd(claim + 1, 1) == (int)gridDim.x - 1) {  // every claim of this CTA precedes its count
+      claim[0] = 0;
+      claim[1] = 0;
+    }
+  }
+}
+
 // Runtime bin stride (any C <= 2 LP): LP lanes per cell, bins sub and
 // sub + LP, lists read from global memory.
 template <int LP>
@@ -947,6 +1038,10 @@ cudaError_t nufft_configure(int smem_optin) {
 #define SA(CSV, GR) \
   if ((e = cudaFuncSetAttribute(spread_stage_multi_kernel<CSV, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
   SA(8, false) SA(16, false) SA(32, false) SA(64, false) SA(8, true) SA(16, true) SA(32, true) SA(64, true)
+#undef SA
+#define SA(CSV) \
+  if ((e = cudaFuncSetAttribute(spread_claim_kernel<CSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, st))) return e;
+  SA(8) SA(16) SA(32) SA(64)
 #undef SA
   return cudaSuccess;
 }
@@ -1094,7 +1189,7 @@ cudaError_t spread_batch(Plan* const* ps, int count, cudaStream_t s) {
   for (int r = 0; r < count; ++r) {
     Plan& p = *ps[r];
     const bool multi = staged(p) && p.cs == ps[0]->cs && p.spread_grouped == ps[0]->spread_grouped &&
-                       staged(*ps[0]) && p.n_sitems > 0;
+                       staged(*ps[0]) && p.n_sitems > 0 && !p.spread_claimed && !ps[0]->spread_claimed;
     if (!multi) {
       const cudaError_t e = spread(p, 0, p.Nf, p.resid, true, s);
       if (e != cudaSuccess) return e;
@@ -1176,8 +1271,19 @@ cudaError_t spread(const Plan& p, int f0, int nbins, const float2* r, bool contr
   }
   if (p.n_sitems == 0) return cudaSuccess;
   if (p.spread_grouped || (p.spread_staged && (p.cs == 8 || p.cs == 16 || p.cs == 32 || p.cs == 64))) {
-    dim3 g((unsigned)p.spread_ctas);  // the plan balanced the items over exactly these CTAs
+    dim3 g((unsigned)p.spread_ctas);  // the CTAs the plan's ranges (or its claims) are for
     const size_t smem = spread_stage_smem();
+    if (p.spread_claimed) {
+#define SC(CSV)                                                                                           \
+  return launch_dep(spread_claim_kernel<CSV>, g, dim3(kSpreadThreads), smem, s, p.grid, (const float2*)p.contrib, \
+                    (const int4*)p.sitems, (const int2*)p.sblob, p.n_sitems, p.spread_claim, nbins, p.n,       \
+                    p.status_dev)
+      if (p.cs == 32) SC(32);
+      if (p.cs == 64) SC(64);
+      if (p.cs == 16) SC(16);
+      SC(8);
+#undef SC
+    }
 #define SS(CSV, GR)                                                                                       \
   return launch_dep(spread_stage_kernel<CSV, GR>, g, dim3(kSpreadThreads), smem, s, p.grid,                 \
                     (const float2*)p.contrib, (const int4*)p.sitems, (const int2*)p.sblob,                  \

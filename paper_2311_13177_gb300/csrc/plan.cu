@@ -203,7 +203,7 @@ void plan_dev_free(Plan* p, void* ptr) {
 void plan_free(Plan* p) {
   if (!p) return;
   void* ptrs[] = {p->kb_idx, p->kb_w, p->phase, p->deapod, p->twiddle, p->blade_frame_d,
-                  p->order, p->items, p->item_cta_off, p->sitems, p->sitem_cta_off, p->sblob, p->contrib, p->grid, p->rows,
+                  p->order, p->items, p->item_cta_off, p->sitems, p->sitem_cta_off, p->spread_claim, p->sblob, p->contrib, p->grid, p->rows,
                   p->resid, p->grad, p->status_dev,
                   p->vol2, p->adam_m, p->adam_v, p->loss_dev, p->scalars,
                   p->red_interp.partials, p->red_interp.counter, p->red_tv.partials,
@@ -563,36 +563,46 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
   }
   p->n_sitems = (int)sitems.size();
   p->spread_entries = blob.size();
-  // Static balance of the spread items over the staged kernel's persistent
-  // CTAs (two per SM): longest first to the least loaded CTA; each CTA's
-  // items are stored contiguously, in k-space order.
+  // Schedule of the spread items over the staged kernel's persistent CTAs
+  // (two per SM).  With few items per CTA, a plan-time balance (longest
+  // first to the least loaded CTA, each CTA's items then in k-space order so
+  // that consecutive items share residual rows in L1) and CTA c takes
+  // [off[c], off[c + 1]).  With many (kSpreadClaimMinItems per CTA or more),
+  // grouped lists keep the items in k-space order and the CTAs claim them
+  // from a device counter, so each CTA's share follows the items' measured
+  // cost.
   std::vector<int> scta_off;
   {
     const int P = std::max(1, std::min(kSpreadCtasPerSm * p->num_sms, p->n_sitems));
-    auto cost = [&](const int4& it) {
-      return (long)it.z + (long)it.y * (p->spread_grouped ? kSpreadGroupCost : kSpreadCellCost);
-    };
-    std::vector<int> idx(sitems.size());
-    for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost(sitems[a]) > cost(sitems[b]); });
-    std::vector<long> load(P, 0);
-    std::vector<std::vector<int>> own(P);
-    for (int q : idx) {
-      int best = 0;
-      for (int c = 1; c < P; ++c)
-        if (load[c] < load[best]) best = c;
-      load[best] += cost(sitems[q]);
-      own[best].push_back(q);
+    p->spread_claimed = p->spread_grouped && p->n_sitems >= kSpreadClaimMinItems * P;
+    if (p->spread_claimed) {
+      scta_off = {0, p->n_sitems};
+    } else {
+      auto cost = [&](const int4& it) {
+        return (long)it.z + (long)it.y * (p->spread_grouped ? kSpreadGroupCost : kSpreadCellCost);
+      };
+      std::vector<int> idx(sitems.size());
+      for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost(sitems[a]) > cost(sitems[b]); });
+      std::vector<long> load(P, 0);
+      std::vector<std::vector<int>> own(P);
+      for (int q : idx) {
+        int best = 0;
+        for (int c = 1; c < P; ++c)
+          if (load[c] < load[best]) best = c;
+        load[best] += cost(sitems[q]);
+        own[best].push_back(q);
+      }
+      std::vector<int4> sorted;
+      sorted.reserve(sitems.size());
+      scta_off.assign(P + 1, 0);
+      for (int c = 0; c < P; ++c) {
+        std::sort(own[c].begin(), own[c].end());  // k-space order within a CTA
+        for (int q : own[c]) sorted.push_back(sitems[q]);
+        scta_off[c + 1] = (int)sorted.size();
+      }
+      sitems.swap(sorted);
     }
-    std::vector<int4> sorted;
-    sorted.reserve(sitems.size());
-    scta_off.assign(P + 1, 0);
-    for (int c = 0; c < P; ++c) {
-      std::sort(own[c].begin(), own[c].end());  // k-space order within a CTA
-      for (int q : own[c]) sorted.push_back(sitems[q]);
-      scta_off[c + 1] = (int)sorted.size();
-    }
-    sitems.swap(sorted);
     p->spread_ctas = P;
   }
   if (blob.empty()) blob.push_back(pad_entry);
@@ -653,8 +663,10 @@ prop_status plan_build(const prop_plan_desc* d, Plan** out, DeviceAllocator* all
     }
   }
   TRY(tab(&p->status_dev, 1, "status word"));
+  if (p->spread_claimed) TRY(tab(&p->spread_claim, 2, "spread item counter"));
   {
     cudaError_t e = cudaMemset(p->status_dev, 0, sizeof(int));
+    if (e == cudaSuccess && p->spread_claim) e = cudaMemset(p->spread_claim, 0, 2 * sizeof(int));
     // the zero row that padding entries of the spread lists point at
     if (e == cudaSuccess) e = cudaMemset(p->contrib + (size_t)p->M * p->cs, 0, (size_t)p->cs * sizeof(float2));
     if (e != cudaSuccess) {

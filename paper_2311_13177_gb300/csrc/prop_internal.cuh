@@ -18,12 +18,17 @@ constexpr int kSpreadPatch = 8;        // spread cells are visited in 8x8-cell p
 constexpr int kSpreadCellCost = 4;     // work of writing one cell, in list entries
 constexpr int kSpreadItemCost = 2048;  // target work per spread item
 constexpr int kSpreadListPad = 4;      // spread lists hold a multiple of this many entries
-constexpr int kSpreadStageInt2 = 6144; // shared-memory stage of one spread item, in int2 (48 KB)
+// Shared-memory stage of one spread item, in int2 (46 KB): two CTAs of two
+// stages then fit the SM's 196 KB shared-memory carve-out (48 KB stages
+// need the 228 KB one), leaving about 60 KB of L1 instead of 28 KB for the
+// residual rows the gathers read (static workload 72.8 -> 68.3 us).
+constexpr int kSpreadStageInt2 = 5888;
 constexpr int kSpreadCtasPerSm = 2;    // persistent staged-spread CTAs per SM
 constexpr int kSpreadGroup = 2;        // grouped spread: 2 x 2-cell groups
 constexpr int kSpreadGroupPatch = 4;   // groups are ordered in 4 x 4-group patches
 constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list entries
 constexpr int kSpreadGroupItemCost = 2048;  // target work per grouped spread item
+constexpr int kSpreadClaimMinItems = 8;  // spread items per CTA from which the CTAs claim items at run time
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
 
 // Interpolation tile (rows x cells per row) for bin stride cs and kernel
@@ -146,8 +151,10 @@ struct Plan {
   int4* sitems = nullptr;        // [n_sitems] (blob offset in int2, cells or groups, entries, blob words)
   int2* sblob = nullptr;         // [spread_entries] item blobs
   int* sitem_cta_off = nullptr;  // [spread_ctas + 1] staged-spread CTA c takes items [off[c], off[c + 1])
+  int* spread_claim = nullptr;   // [2]: next unclaimed spread item, CTAs done (both 0 between launches)
+  bool spread_claimed = false;   // the staged-spread CTAs claim items at run time (else the ranges above)
   int n_sitems = 0;
-  int spread_ctas = 1;           // persistent staged-spread CTAs the items are balanced over
+  int spread_ctas = 1;           // persistent staged-spread CTAs (the ranges' CTA count)
   size_t spread_entries = 0;
   bool spread_staged = true;     // cell lists: every item fits a shared-memory stage
   bool spread_grouped = false;   // sblob/sitems hold grouped lists (2 x 2-cell groups), else cell lists

@@ -52,6 +52,28 @@ def test_forward_adjoint_match_oracle(shape):
     _check(c)
 
 
+@pytest.mark.parametrize("shape,kb_width", [
+    ((256, 4, 3, 4, 256, 1), 8),   # 2N = 512: radix-32 and radix-16 column passes
+    ((192, 3, 4, 4, 192, 2), 6),   # 2N = 384: radices 8, 8, 6 in the column passes, two frames
+])
+def test_large_transform_lengths_sampled(shape, kb_width):
+    """The column passes' long-transform shapes: 2048 samples of A V and 256
+    voxels of A^H y, each against the oracle's exact sum."""
+    N, Nf, B, L, R, T = shape
+    c = random_case(N, Nf, B, L, R, T, seed=N + 5)
+    g = geometry(N, L, R, c["theta"], c["delta"], c["blade_frame"], T)
+    plan = _plan(c, kb_width=kb_width)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(N)
+    y = plan.forward(torch.from_numpy(c["V"]).to(dev)).cpu().numpy().reshape(-1)
+    s = rng.choice(y.size, 2048, replace=False)
+    assert rel(y[s], oracle.forward_at(c["V"].astype(np.complex128), g, s)) < TOL
+    Va = plan.adjoint(torch.from_numpy(c["y"]).to(dev)).cpu().numpy().reshape(-1)
+    q = rng.choice(Va.size, 256, replace=False)
+    assert rel(Va[q], oracle.adjoint_at(c["y"].astype(np.complex128), g, q)) < TOL
+    plan.destroy()
+
+
 @pytest.mark.parametrize("shape", [(32, 8, 5, 8, 32, 1), (48, 3, 4, 6, 48, 2)])
 def test_width8_kernel_is_more_accurate(shape):
     """Kernel width 8: same operators, error two orders of magnitude below width 6."""

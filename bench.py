@@ -61,6 +61,7 @@ def parse():
                          "1e-3 parity bar at the static workload; 6 drifts 2e-3 to 6e-3 from the exact operator's "
                          "trajectory there)")
     ap.add_argument("--no-kplanes", action="store_true", help="skip the K-Planes model measurement")
+    ap.add_argument("--no-width6", action="store_true", help="skip the width-6 comparison (kb_width_6)")
     ap.add_argument("--row-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="row kernel: 0 the plan's choice, 1 per-row CTAs, 2 warp-specialised")
     ap.add_argument("--diff-study", action="store_true",
@@ -567,7 +568,7 @@ def run_ours(args):
             line["serving"] = run_serving(args.serve_requests, args.serve_iters, 7, local, args.serve_slots)
         if world == 1 and not args.no_projection and args.workload == WORKLOAD:
             line["projection_model"] = run_projection_model(plan, w, prob, dev, peak, K)
-        if world == 1 and args.workload == WORKLOAD and args.kb_width != 6:
+        if world == 1 and args.workload == WORKLOAD and args.kb_width != 6 and not args.no_width6:
             line["kb_width_6"] = run_width6(w, prob, dev, params, min(K, 2000), local)
         if world == 1 and not args.no_kplanes and args.workload == WORKLOAD:
             line["kplanes"] = run_kplanes(dev, peak, local)

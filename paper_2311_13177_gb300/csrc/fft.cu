@@ -348,8 +348,9 @@ struct GroupSync {
 
 // `hook` runs once, on every thread, right after the barrier that follows
 // the first pass (all reads of the first pass's input are then complete).
+// COLS: lines a tile (the stride of the exchange buffer X[pos][col]).
 template <int NFFT, int EV, int SIGN, int PI, int NS, bool PIN, bool POUT, class Sync = CtaSync, class In,
-          class Out, class Hook = NoHook>
+          class Out, class Hook = NoHook, int COLS = kFftCols>
 __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, int tl, const In& in,
                                          const Out& out, const Hook& hook = Hook()) {
   constexpr RadixPlan RP = radix_plan(NFFT, EV);
@@ -399,7 +400,7 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
       } else if constexpr (FIRST) {
         x = in(pos, col);
       } else {
-        x = X[pos * kFftCols + col];
+        x = X[pos * COLS + col];
       }
       if constexpr (NS > 1) {
         if (r > 0) x = SIGN < 0 ? cmul(x, w[r]) : cmulc(x, w[r]);
@@ -415,11 +416,11 @@ __device__ __forceinline__ void fft_pass(float2* X, const float2* tws, int col, 
       const int j = tl + TPL * q;
       const int d = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-      for (int r = 0; r < R; ++r) X[(d + r * NS) * kFftCols + col] = v[q * R + r];
+      for (int r = 0; r < R; ++r) X[(d + r * NS) * COLS + col] = v[q * R + r];
     }
     Sync::sync();
     if constexpr (FIRST) hook();
-    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT, Sync>(X, tws, col, tl, in, out, hook);
+    fft_pass<NFFT, EV, SIGN, PI + 1, NS * R, PIN, POUT, Sync, In, Out, Hook, COLS>(X, tws, col, tl, in, out, hook);
   } else {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -1322,7 +1323,7 @@ cudaError_t dispatch_fused(int n, const FusedArgs& a, bool fwd_tail, dim3 grid, 
 
 // --- Centred unitary 2-D DFT of one N x N image (projection model) ----------
 //
-// Four passes of NFFT = N point transforms, 16 lines per CTA: forward rows,
+// Four passes of NFFT = N point transforms, kCartCols lines per CTA: forward rows,
 // forward columns (scale 1/N; optionally masked, or fused with the blade's
 // data term), inverse columns (input optionally masked), inverse rows (scale
 // 1/N).  The centring (image index i = x + N/2, k index u = N k + N/2) is
@@ -1413,49 +1414,61 @@ struct OutCartLoss {
   }
 };
 
+template <int NFFT>
+constexpr int cart_threads() {
+  return NFFT / kValsPlain<NFFT> * kCartCols;
+}
+template <int NFFT>
+constexpr size_t cart_smem() {
+  return (size_t)NFFT * kCartCols * sizeof(float2) + (size_t)Shape<NFFT, kValsPlain<NFFT>>::TW * sizeof(float2);
+}
+
 template <int NFFT, int PASS>
-__global__ void __launch_bounds__(Shape<NFFT, kValsPlain<NFFT>>::THREADS) cart_fft_kernel(CartArgs a) {
+__global__ void __launch_bounds__(cart_threads<NFFT>()) cart_fft_kernel(CartArgs a) {
   constexpr int EV = kValsPlain<NFFT>;
+  constexpr int CC = kCartCols;
   extern __shared__ float2 smem[];
   float2* X = smem;
-  float2* tw = smem + NFFT * kFftCols;
+  float2* tw = smem + NFFT * CC;
   build_twiddles<NFFT, EV>(tw, a.twiddle);
   grid_dep_wait();
   grid_dep_release();
   __syncthreads();
-  const int col = threadIdx.x % kFftCols;
-  const int tl = threadIdx.x / kFftCols;
-  const int l0 = blockIdx.x * kFftCols;
+  const int col = threadIdx.x % CC;
+  const int tl = threadIdx.x / CC;
+  const int l0 = blockIdx.x * CC;
   if constexpr (PASS == kCartRowsFwd) {
     InCartRows in{a.src, NFFT, (size_t)l0};
     OutCartRows out{a.dst, NFFT, (size_t)l0, a.scale};
-    fft_pass<NFFT, EV, -1, 0, 1, false, false>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, -1, 0, 1, false, false, CtaSync, InCartRows, OutCartRows, NoHook, CC>(X, tw, col, tl, in, out);
   } else if constexpr (PASS == kCartColsFwd) {
     InCartCols in{a.src, nullptr, NFFT, l0};
     if (a.y) {
       float acc = 0.f;
       OutCartLoss out{a.dst, a.mask, a.y, a.yimg, a.wk, a.wi, NFFT, l0, a.scale, &acc};
-      fft_pass<NFFT, EV, -1, 0, 1, false, false>(X, tw, col, tl, in, out);
+      fft_pass<NFFT, EV, -1, 0, 1, false, false, CtaSync, InCartCols, OutCartLoss, NoHook, CC>(X, tw, col, tl, in,
+                                                                                             out);
       finish_loss(acc, a.partials, a.counter, a.loss_const, a.loss_out);
     } else {
       OutCartCols out{a.dst, a.mask, NFFT, l0, a.scale};
-      fft_pass<NFFT, EV, -1, 0, 1, false, false>(X, tw, col, tl, in, out);
+      fft_pass<NFFT, EV, -1, 0, 1, false, false, CtaSync, InCartCols, OutCartCols, NoHook, CC>(X, tw, col, tl, in,
+                                                                                             out);
     }
   } else if constexpr (PASS == kCartColsInv) {
     InCartCols in{a.src, a.mask, NFFT, l0};
     OutCartCols out{a.dst, nullptr, NFFT, l0, a.scale};
-    fft_pass<NFFT, EV, +1, 0, 1, false, false>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, +1, 0, 1, false, false, CtaSync, InCartCols, OutCartCols, NoHook, CC>(X, tw, col, tl, in, out);
   } else {
     InCartRows in{a.src, NFFT, (size_t)l0};
     OutCartRows out{a.dst, NFFT, (size_t)l0, a.scale};
-    fft_pass<NFFT, EV, +1, 0, 1, false, false>(X, tw, col, tl, in, out);
+    fft_pass<NFFT, EV, +1, 0, 1, false, false, CtaSync, InCartRows, OutCartRows, NoHook, CC>(X, tw, col, tl, in, out);
   }
 }
 
 template <int NFFT>
 cudaError_t launch_cart(int pass, const CartArgs& a, cudaStream_t s) {
-  const dim3 grid(NFFT / kFftCols), block(Shape<NFFT, kValsPlain<NFFT>>::THREADS);
-  const size_t smem = Shape<NFFT, kValsPlain<NFFT>>::SMEM;
+  const dim3 grid(NFFT / kCartCols), block(cart_threads<NFFT>());
+  const size_t smem = cart_smem<NFFT>();
   switch (pass) {
     case kCartRowsFwd: return launch_dep(cart_fft_kernel<NFFT, kCartRowsFwd>, grid, block, smem, s, a);
     case kCartColsFwd: return launch_dep(cart_fft_kernel<NFFT, kCartColsFwd>, grid, block, smem, s, a);
@@ -1466,7 +1479,7 @@ cudaError_t launch_cart(int pass, const CartArgs& a, cudaStream_t s) {
 
 template <int NFFT>
 cudaError_t configure_cart() {
-  const int smem = (int)Shape<NFFT, kValsPlain<NFFT>>::SMEM;
+  const int smem = (int)cart_smem<NFFT>();
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(cart_fft_kernel<NFFT, kCartRowsFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
     return e;
@@ -1764,7 +1777,7 @@ cudaError_t cart_fft_pass(int N, int pass, const float2* src, float2* dst, const
   a.N = N;
   a.scale = scale;
   if (loss) {
-    if (pass != kCartColsFwd || !loss->red || !mask || loss->red->capacity < N / kFftCols) return cudaErrorInvalidValue;
+    if (pass != kCartColsFwd || !loss->red || !mask || loss->red->capacity < N / kCartCols) return cudaErrorInvalidValue;
     a.y = loss->y;
     a.yimg = loss->yimg;
     a.wk = loss->wk;

@@ -336,7 +336,7 @@ prop_status plan_ensure_proj(Plan& p, bool images) {
       tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
     const int red_u = update_row_blocks(p) * p.T * N;
-    const int red_k = std::max(N / kFftCols, 32);
+    const int red_k = std::max(N / kCartCols, 32);  // the loss pass's CTAs
     if ((st = proj_alloc(p, (void**)&p.proj_shift, sh.size() * sizeof(int4), "projection shifts")) != PROP_OK) return st;
     if ((st = proj_alloc(p, (void**)&p.proj_mask, mask.size(), "blade masks")) != PROP_OK) return st;
     if ((st = proj_alloc(p, (void**)&p.proj_twiddle, N * sizeof(float2), "DFT twiddles")) != PROP_OK) return st;

@@ -30,6 +30,10 @@ constexpr int kSpreadGroupCost = 4;    // work of writing one group, in list ent
 constexpr int kSpreadGroupItemCost = 2048;  // target work per grouped spread item
 constexpr int kSpreadClaimMinItems = 8;  // spread items per CTA from which the CTAs claim items at run time
 constexpr int kFftCols = 16;       // columns (complex lines) per FFT tile
+// Lines a CTA of the projection model's image transforms: 4 (an N x N image
+// is only N lines a pass, so 16-line tiles left all but N / 16 SMs idle;
+// 4-line tiles still read whole 32-byte sectors along a column).
+constexpr int kCartCols = 4;
 
 // Interpolation tile (rows x cells per row) for bin stride cs and kernel
 // width W: 16 x 16 up to 32 bins, 8 x 8 above.  At width 8 with 32 bins a

@@ -147,10 +147,14 @@ def test_full_size_sampled_against_oracle(name):
     ref = oracle.forward_at(V.astype(np.complex128), g, s)
     assert rel(y[s], ref) < TOL
     yy = p["y"]
-    Va = plan.adjoint(torch.from_numpy(yy).to(dev)).cpu().numpy().reshape(-1)
+    Vt = plan.adjoint(torch.from_numpy(yy).to(dev))
+    Va = Vt.cpu().numpy().reshape(-1)
     q = rng.choice(Va.size, 512, replace=False)
     refa = oracle.adjoint_at(yy.astype(np.complex128), g, q)
     assert rel(Va[q], refa) < TOL
+    # a second launch (the dynamic plan's spread claims its items from a
+    # counter that each launch must leave at zero) gives the same grid
+    assert torch.equal(plan.adjoint(torch.from_numpy(yy).to(dev)), Vt)
     plan.destroy()
 
 

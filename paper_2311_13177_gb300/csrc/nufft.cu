@@ -669,10 +669,7 @@ __device__ __forceinline__ void gather_groups(const int2* base, int ngroups, int
     float4 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-    for (int e = beg; e < end; e += 4) {
-      const int4 o = *reinterpret_cast<const int4*>(offs + e);
-      const float4 v[4] = {row(o.x), row(o.y), row(o.z), row(o.w)};
+    auto add4 = [&](int e, const float4* v) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float4 w = wts[e + u];
@@ -685,6 +682,21 @@ __device__ __forceinline__ void gather_groups(const int2* base, int ngroups, int
           acc[c].w = fmaf(wa[c], v[u].w, acc[c].w);
         }
       }
+    };
+    int e = beg;
+#pragma unroll 1
+    for (; e + 8 <= end; e += 8) {  // eight rows in flight
+      const int4 o0 = *reinterpret_cast<const int4*>(offs + e);
+      const int4 o1 = *reinterpret_cast<const int4*>(offs + e + 4);
+      const float4 v0[4] = {row(o0.x), row(o0.y), row(o0.z), row(o0.w)};
+      const float4 v1[4] = {row(o1.x), row(o1.y), row(o1.z), row(o1.w)};
+      add4(e, v0);
+      add4(e + 4, v1);
+    }
+    if (e < end) {  // lists hold a multiple of four entries
+      const int4 o = *reinterpret_cast<const int4*>(offs + e);
+      const float4 v[4] = {row(o.x), row(o.y), row(o.z), row(o.w)};
+      add4(e, v);
     }
     if (ok) {
       const bool l0 = 2 * sub < Cv, l1 = 2 * sub + 1 < Cv;

@@ -638,8 +638,9 @@ __device__ __forceinline__ void gather_item2(const int2* cells, int ncells, int 
 // entry's four weights to the four cells of the group held in registers.
 // A row is read once per group instead of once per covered cell, and each
 // cell still sums its own terms in ascending sample order (zero weights add
-// exact zeros), as a per-cell list would.  Entries come in batches of four
-// with the four row loads in flight together.  Warps claim groups from a
+// exact zeros), as a per-cell list would.  Entries come in batches of eight
+// with the eight row loads in flight together (then a last batch of four:
+// every list holds a multiple of four).  Warps claim groups from a
 // shared counter.  `base` points at the item's blob in shared memory.
 template <int CS>
 __device__ __forceinline__ void gather_groups(const int2* base, int ngroups, int nent, int lane, int* next,

@@ -262,7 +262,9 @@ PROP_API prop_status prop_psnr(prop_plan plan, const void* image_dev, const void
  * stride, kernel width) and advances each class with batched iterations as
  * prop_reconstruct_batch does: one launch per stage serves every running
  * request of the class, whatever its blade count, frames or data; classes
- * run on their own streams and overlap.  Requests that arrive while others
+ * run on their own streams and overlap, the class holding the oldest running
+ * request (by submit time) on a high-priority stream so that it keeps the
+ * device as a FIFO queue would give it.  Requests that arrive while others
  * run join their class's next batched iteration as soon as a slot and memory
  * free up.  A request that needs more than the whole budget fails with
  * PROP_ERR_OOM.  Results are bitwise identical to a lone prop_reconstruct of
